@@ -1,0 +1,116 @@
+"""Plant plausible mistakes in the oracle (on the CPU) and check that a pin catches each.
+
+Each case replaces one oracle function with a subtly wrong version and runs the
+pins that should notice; the case passes when at least one of them fails.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import stem as O
+import tests.test_oracle_pins as pins
+
+
+def _fails(fn, *args):
+    try:
+        fn(*args)
+    except AssertionError:
+        return True
+    return False
+
+
+def _prop_flipped(p):
+    return np.conj(O._orig_propagator(p))
+
+
+def _prop_unmasked(p):
+    m = O.freq_index(p.n).astype(np.float64)
+    kx = m / p.cell[0]
+    ky = m / p.cell[1]
+    k2 = kx[None, :] ** 2 + ky[:, None] ** 2
+    return np.exp(-1j * math.pi * p.lam * p.slice_dz * k2)
+
+
+def _prop_xy_swapped(p):
+    m = O.freq_index(p.n).astype(np.float64)
+    kx = m / p.cell[1]
+    ky = m / p.cell[0]
+    k2 = kx[None, :] ** 2 + ky[:, None] ** 2
+    return np.exp(-1j * math.pi * p.lam * p.slice_dz * k2) * O.bandlimit_mask(p.n)
+
+
+def _trans_flipped(p, v):
+    return np.exp(-1j * p.sigma * v)
+
+
+def _angle_xy_swapped(p):
+    m = O.freq_index(p.n).astype(np.float64)
+    kx = m / p.cell[1]
+    ky = m / p.cell[0]
+    return p.lam * np.sqrt(kx[None, :] ** 2 + ky[:, None] ** 2) * 1000.0
+
+
+def _probe_unnormalised(p, xy):
+    return O._orig_probe_k(p, xy) * math.sqrt(int(O.aperture(p).sum()))
+
+
+def _origin_round_down(p, f, xy):
+    w = p.n // f
+    xy = np.atleast_2d(xy)
+    ox = np.floor(xy[:, 0] / p.dx).astype(np.int64) - w // 2
+    oy = np.floor(xy[:, 1] / p.dy).astype(np.int64) - w // 2
+    return np.stack([np.mod(ox, p.n), np.mod(oy, p.n)], axis=1)
+
+
+def _coef_conj(p, beams, xy):
+    return np.conj(O._orig_prism_coefficients(p, beams, xy))
+
+
+def _slice_round(p, z):
+    return np.clip(np.round(np.asarray(z) / p.slice_dz).astype(np.int64), 0, p.n_slices - 1)
+
+
+def _potential_one_gaussian(p, xyz, gauss):
+    g = np.array(gauss, dtype=np.float32).copy()
+    g[:, 2] = 0.0
+    return O._orig_projected_potential(p, xyz, g)
+
+
+def _lambda_nonrel(e):
+    return O.HC_KEV_A / math.sqrt(2.0 * O.MC2_KEV * e)
+
+
+def _ms_last_slice_unpropagated(p, trans, psi):
+    prop = O.propagator(p)
+    psi = np.asarray(psi, dtype=np.complex128)
+    for s in range(p.n_slices):
+        if s < p.n_slices - 1:
+            psi = np.fft.ifft2(prop * np.fft.fft2(trans[s] * psi, axes=(-2, -1)), axes=(-2, -1))
+        else:
+            return O.bandlimit_mask(p.n) * np.fft.fft2(trans[s] * psi, axes=(-2, -1))
+
+
+CASES = [
+    ("propagator", _prop_flipped, [pins.test_phase_grating_one_slice_jacobi_anger,
+                                   pins.test_gaussian_beam_fresnel_closed_form]),
+    ("propagator", _prop_unmasked, [pins.test_norm_loss_equals_masked_energy_parseval]),
+    ("propagator", _prop_xy_swapped, [pins.test_phase_grating_one_slice_jacobi_anger]),
+    ("transmission", _trans_flipped, [pins.test_phase_grating_one_slice_jacobi_anger]),
+    ("angle_mrad", _angle_xy_swapped, [pins.test_ring_table_orientation_hand_values]),
+    ("probe_k", _probe_unnormalised, [pins.test_probe_normalisation_and_free_space_rings]),
+    ("prism_window_origin", _origin_round_down, [pins.test_prism_window_origin]),
+    ("prism_coefficients", _coef_conj, [pins.test_prism_f1_equals_multislice]),
+    ("slice_index", _slice_round, [pins.test_slice_assignment]),
+    ("projected_potential", _potential_one_gaussian, [pins.test_potential_sum_rule_and_peak]),
+    ("wavelength", _lambda_nonrel, [pins.test_wavelength_textbook_values]),
+    ("multislice_k", _ms_last_slice_unpropagated, [pins.test_phase_grating_one_slice_jacobi_anger]),
+]
+
+
+@pytest.mark.parametrize("name,mutant,checks", CASES, ids=[f"{c[0]}:{c[1].__name__}" for c in CASES])
+def test_pins_catch_planted_mistake(monkeypatch, name, mutant, checks):
+    monkeypatch.setattr(O, "_orig_" + name, getattr(O, name), raising=False)
+    monkeypatch.setattr(O, name, mutant)
+    caught = [c.__name__ for c in checks if _fails(c)]
+    assert caught, f"no pin caught the mutation {mutant.__name__} of {name}"

@@ -1,0 +1,442 @@
+// api.cu - the C ABI of libstem (declared in include/stem.h).
+//
+// Host code here validates arguments, builds the plan's small tables (FP64
+// decisions of aperture, band limit and ring membership; propagator factors;
+// PRISM beam lists) and sequences the kernels on the caller's stream.  No
+// simulation arithmetic runs on the host.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "internal.h"
+
+using namespace stem;
+
+namespace {
+
+// CODATA 2018: h*c in keV*A and the electron rest energy in keV.
+constexpr double kHcKevA = 12.398419843320026;
+constexpr double kMc2Kev = 510.99895000;
+
+double wavelength_a(double e_kev) { return kHcKevA / std::sqrt(e_kev * (2.0 * kMc2Kev + e_kev)); }
+
+double interaction_sigma(double e_kev) {
+  const double lam = wavelength_a(e_kev);
+  return (2.0 * M_PI / (lam * e_kev * 1000.0)) * (kMc2Kev + e_kev) / (2.0 * kMc2Kev + e_kev);
+}
+
+int freq(int j, int n) { return j < n / 2 ? j : j - n; }
+
+bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+int log2i(int n) {
+  int l = 0;
+  while ((1 << l) < n) ++l;
+  return l;
+}
+
+cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
+
+stem_status cuda_status(cudaError_t e) { return e == cudaSuccess ? STEM_OK : STEM_ERR_CUDA; }
+
+stem_status check_params(const stem_params* p) {
+  if (!p) return STEM_ERR_INVALID;
+  if (!is_pow2(p->n) || p->n < 8 || p->n > 2048) return STEM_ERR_UNSUPPORTED;
+  if (!(p->cell[0] > 0.0) || !(p->cell[1] > 0.0) || p->n_slices < 1 || !(p->slice_dz > 0.0) ||
+      !(p->energy_kev > 0.0) || !(p->alpha_mrad >= 0.0) || !(p->ring_width_mrad > 0.0) || p->n_rings < 1 ||
+      p->n_rings > kMaxRings)
+    return STEM_ERR_INVALID;
+  return STEM_OK;
+}
+
+// f must be a power of two with W = n / f >= 8.
+bool f_ok(const stem_plan_s* pl, int f) { return is_pow2(f) && f <= pl->n / 8; }
+
+// Number of beams of the FP64 aperture test for a given f (used by the footprint query).
+int count_beams(const stem_params* p, int f, double lam) {
+  const int n = p->n;
+  int nb = 0;
+  for (int nn = -n / 2; nn < n / 2; ++nn) {
+    if (((nn % f) + f) % f) continue;
+    for (int mm = -n / 2; mm < n / 2; ++mm) {
+      if (((mm % f) + f) % f) continue;
+      if (9LL * ((long long)mm * mm + (long long)nn * nn) > (long long)n * n) continue;
+      const double kx = (double)mm / p->cell[0], ky = (double)nn / p->cell[1];
+      if ((lam * std::sqrt(kx * kx + ky * ky)) * 1000.0 <= p->alpha_mrad) ++nb;
+    }
+  }
+  return nb;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* stem_status_string(stem_status s) {
+  switch (s) {
+    case STEM_OK: return "ok";
+    case STEM_ERR_INVALID: return "invalid argument";
+    case STEM_ERR_NOMEM: return "out of memory or workspace too small";
+    case STEM_ERR_CUDA: return "CUDA error";
+    case STEM_ERR_UNSUPPORTED: return "unsupported size";
+    case STEM_ERR_TIMEOUT: return "device wait timed out";
+    default: return "unknown status";
+  }
+}
+
+void stem_plan_destroy(stem_plan pl) {
+  if (!pl) return;
+  cudaFree(pl->prop_x);
+  cudaFree(pl->prop_y);
+  for (int i = 0; i <= kMaxLog2F; ++i) {
+    cudaFree(pl->lut[i]);
+    cudaFree(pl->beams[i]);
+  }
+  delete pl;
+}
+
+stem_status stem_plan_create(const stem_params* params, stem_plan* out) {
+  if (!out) return STEM_ERR_INVALID;
+  *out = nullptr;
+  stem_status st = check_params(params);
+  if (st != STEM_OK) return st;
+  stem_plan_s* pl = new (std::nothrow) stem_plan_s;
+  if (!pl) return STEM_ERR_NOMEM;
+  pl->p = *params;
+  const int n = params->n;
+  pl->n = n;
+  pl->lam = wavelength_a(params->energy_kev);
+  pl->sigma = interaction_sigma(params->energy_kev);
+  cudaGetDevice(&pl->device);
+  const double lx = params->cell[0], ly = params->cell[1];
+
+  // Fine look-up table: aperture bit and ring index, decided in FP64.
+  std::vector<uint16_t> lut((size_t)n * n);
+  int n_ap = 0;
+  for (int i = 0; i < n; ++i) {
+    const int nn = freq(i, n);
+    const double ky = (double)nn / ly;
+    for (int j = 0; j < n; ++j) {
+      const int mm = freq(j, n);
+      const double kx = (double)mm / lx;
+      const bool mask = 9LL * ((long long)mm * mm + (long long)nn * nn) <= (long long)n * n;
+      const double k = std::sqrt(kx * kx + ky * ky);
+      const double ang = (pl->lam * k) * 1000.0;
+      uint16_t v = kLutNoRing;
+      if (mask) {
+        const double r = std::floor(ang / params->ring_width_mrad);
+        if (r < (double)params->n_rings) v = (uint16_t)r;
+        if (ang <= params->alpha_mrad) {
+          v |= kLutAperture;
+          ++n_ap;
+        }
+      }
+      lut[(size_t)i * n + j] = v;
+    }
+  }
+  pl->n_aperture = n_ap;
+
+  // Propagator factors exp(-i pi lambda dz (m/L)^2) per axis (Eq. 2 is separable).
+  std::vector<float2> px(n), py(n);
+  for (int j = 0; j < n; ++j) {
+    const double kx = (double)freq(j, n) / lx, ky = (double)freq(j, n) / ly;
+    const double ax = -M_PI * pl->lam * params->slice_dz * kx * kx;
+    const double ay = -M_PI * pl->lam * params->slice_dz * ky * ky;
+    px[j] = make_float2((float)std::cos(ax), (float)std::sin(ax));
+    py[j] = make_float2((float)std::cos(ay), (float)std::sin(ay));
+  }
+
+  cudaError_t e = cudaSuccess;
+  auto upload = [&](void** dst, const void* src, size_t bytes) {
+    if (e != cudaSuccess) return;
+    e = cudaMalloc(dst, bytes > 0 ? bytes : 16);
+    if (e == cudaSuccess && bytes > 0) e = cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice);
+  };
+  upload(reinterpret_cast<void**>(&pl->prop_x), px.data(), n * sizeof(float2));
+  upload(reinterpret_cast<void**>(&pl->prop_y), py.data(), n * sizeof(float2));
+
+  for (int lf = 0; lf <= kMaxLog2F; ++lf) {
+    const int f = 1 << lf;
+    if (f > n / 8) break;
+    const int w = n / f;
+    // coarse table: window frequency (mu, nu) is the fine frequency (f mu, f nu)
+    std::vector<uint16_t> coarse((size_t)w * w);
+    for (int v = 0; v < w; ++v) {
+      const int fi = ((f * freq(v, w)) % n + n) % n;
+      for (int u = 0; u < w; ++u) {
+        const int fj = ((f * freq(u, w)) % n + n) % n;
+        coarse[(size_t)v * w + u] = lut[(size_t)fi * n + fj];
+      }
+    }
+    upload(reinterpret_cast<void**>(&pl->lut[lf]), coarse.data(), coarse.size() * sizeof(uint16_t));
+    // PRISM beams: aperture pixels on every f-th frequency, ordered by n then m.
+    std::vector<int2>& bl = pl->h_beams[lf];
+    for (int nn = -n / 2; nn < n / 2; ++nn) {
+      if (((nn % f) + f) % f) continue;
+      for (int mm = -n / 2; mm < n / 2; ++mm) {
+        if (((mm % f) + f) % f) continue;
+        const int i = (nn + n) % n, j = (mm + n) % n;
+        if (lut[(size_t)i * n + j] & kLutAperture) bl.push_back(make_int2(mm, nn));
+      }
+    }
+    pl->n_beams[lf] = (int)bl.size();
+    upload(reinterpret_cast<void**>(&pl->beams[lf]), bl.data(), bl.size() * sizeof(int2));
+  }
+  if (e != cudaSuccess) {
+    stem_plan_destroy(pl);
+    return e == cudaErrorMemoryAllocation ? STEM_ERR_NOMEM : STEM_ERR_CUDA;
+  }
+  *out = pl;
+  return STEM_OK;
+}
+
+stem_status stem_plan_constants(stem_plan pl, double* lambda_a, double* sigma, int32_t* n_aperture) {
+  if (!pl) return STEM_ERR_INVALID;
+  if (lambda_a) *lambda_a = pl->lam;
+  if (sigma) *sigma = pl->sigma;
+  if (n_aperture) *n_aperture = pl->n_aperture;
+  return STEM_OK;
+}
+
+// ----------------------------------------------------------------------------- potentials
+size_t stem_slice_potentials_workspace(stem_plan pl, int64_t n_atoms) {
+  (void)pl;
+  return potential_workspace(n_atoms);
+}
+
+stem_status stem_slice_potentials(stem_plan pl, const double* xyz, const float* gauss, int64_t n_atoms, float* v_out,
+                                  void* trans_out, void* ws, size_t ws_bytes, void* stream) {
+  if (!pl || n_atoms < 0 || (n_atoms > 0 && (!xyz || !gauss)) || (!v_out && !trans_out) || !ws)
+    return STEM_ERR_INVALID;
+  if (pl->n < 64) return STEM_ERR_UNSUPPORTED;
+  if (ws_bytes < potential_workspace(n_atoms)) return STEM_ERR_NOMEM;
+  return cuda_status(launch_potentials(pl->p, pl->sigma, xyz, gauss, n_atoms, v_out,
+                                       static_cast<float2*>(trans_out), ws, as_stream(stream)));
+}
+
+// ----------------------------------------------------------------------------- multislice
+size_t stem_multislice_workspace(stem_plan pl, int32_t batch) {
+  if (!pl || batch < 1) return 0;
+  return (size_t)batch * pl->n * pl->n * sizeof(float2);
+}
+
+stem_status stem_multislice_scan(stem_plan pl, const void* trans, const double* probe_xy, int64_t n_probes,
+                                 int32_t batch, float weight, float* rings_out, void* ws, size_t ws_bytes,
+                                 void* stream) {
+  if (!pl || !trans || n_probes < 0 || (n_probes > 0 && (!probe_xy || !rings_out)) || batch < 1 || batch > 65535 ||
+      !ws)
+    return STEM_ERR_INVALID;
+  const int n = pl->n;
+  if (n < 64) return STEM_ERR_UNSUPPORTED;
+  if (ws_bytes < stem_multislice_workspace(pl, batch)) return STEM_ERR_NOMEM;
+  cudaStream_t s = as_stream(stream);
+  const size_t plane = (size_t)n * n;
+  PassArgs a;
+  a.wave = static_cast<float2*>(ws);
+  a.prop_x = pl->prop_x;
+  a.prop_y = pl->prop_y;
+  a.prop_scale = 1.0f / (float)plane;
+  a.lut = pl->lut[0];
+  a.n_rings = pl->p.n_rings;
+  a.ring_scale = weight;
+  a.inv_lx = 1.0 / pl->p.cell[0];
+  a.inv_ly = 1.0 / pl->p.cell[1];
+  a.probe_norm = (float)(1.0 / (std::sqrt((double)std::max(pl->n_aperture, 1)) * (double)plane));
+  const float2* t = static_cast<const float2*>(trans);
+  for (int64_t p0 = 0; p0 < n_probes; p0 += batch) {
+    a.batch = (int)std::min<int64_t>(batch, n_probes - p0);
+    a.probe_xy = probe_xy + 2 * p0;
+    a.rings = rings_out + p0 * pl->p.n_rings;
+    cudaError_t e = launch_col_pass(n, COL_PROBE_INIT, a, s);
+    for (int sl = 0; sl < pl->p.n_slices && e == cudaSuccess; ++sl) {
+      a.trans = t + sl * plane;
+      e = launch_row_pass(n, ROW_SLICE, a, s);
+      if (e == cudaSuccess) e = launch_col_pass(n, sl + 1 < pl->p.n_slices ? COL_SLICE : COL_DET, a, s);
+    }
+    if (e != cudaSuccess) return STEM_ERR_CUDA;
+  }
+  return STEM_OK;
+}
+
+// ----------------------------------------------------------------------------- PRISM S-matrix
+stem_status stem_prism_beams(stem_plan pl, int32_t f, int32_t* n_beams, int32_t* mn_host) {
+  if (!pl || !n_beams || !f_ok(pl, f)) return STEM_ERR_INVALID;
+  const int lf = log2i(f);
+  *n_beams = pl->n_beams[lf];
+  if (mn_host)
+    for (int b = 0; b < pl->n_beams[lf]; ++b) {
+      mn_host[2 * b] = pl->h_beams[lf][b].x;
+      mn_host[2 * b + 1] = pl->h_beams[lf][b].y;
+    }
+  return STEM_OK;
+}
+
+size_t stem_prism_smatrix_bytes(stem_plan pl, int32_t f, stem_storage storage) {
+  if (!pl || !f_ok(pl, f) || storage < STEM_F32 || storage > STEM_BF16) return 0;
+  return smatrix_layout(pl->n, pl->n_beams[log2i(f)], storage).total;
+}
+
+static size_t smatrix_ws_waves(int n, int batch) { return ((size_t)batch * n * n * sizeof(float2) + 255) / 256 * 256; }
+
+size_t stem_prism_smatrix_workspace(stem_plan pl, int32_t batch) {
+  if (!pl || batch < 1) return 0;
+  return smatrix_ws_waves(pl->n, batch) + (size_t)batch * sizeof(unsigned);
+}
+
+stem_status stem_prism_smatrix(stem_plan pl, const void* trans, int32_t f, stem_storage storage, int32_t batch,
+                               void* smatrix, size_t smatrix_bytes, void* ws, size_t ws_bytes, void* stream) {
+  if (!pl || !trans || !smatrix || !ws || !f_ok(pl, f) || storage < STEM_F32 || storage > STEM_BF16 || batch < 1 ||
+      batch > 65535)
+    return STEM_ERR_INVALID;
+  const int n = pl->n;
+  if (n < 64) return STEM_ERR_UNSUPPORTED;
+  const int lf = log2i(f);
+  const int nb = pl->n_beams[lf];
+  const SmatLayout L = smatrix_layout(n, nb, storage);
+  if (smatrix_bytes < L.total || ws_bytes < stem_prism_smatrix_workspace(pl, batch)) return STEM_ERR_NOMEM;
+  if (reinterpret_cast<uintptr_t>(smatrix) % 256) return STEM_ERR_INVALID;
+  cudaStream_t s = as_stream(stream);
+  const size_t plane = (size_t)n * n;
+  PassArgs a;
+  a.wave = static_cast<float2*>(ws);
+  a.prop_x = pl->prop_x;
+  a.prop_y = pl->prop_y;
+  a.prop_scale = 1.0f / (float)plane;
+  a.beam_max = reinterpret_cast<unsigned*>(static_cast<char*>(ws) + smatrix_ws_waves(n, batch));
+  const float2* t = static_cast<const float2*>(trans);
+  for (int b0 = 0; b0 < nb; b0 += batch) {
+    a.batch = std::min(batch, nb - b0);
+    a.beams = pl->beams[lf] + b0;
+    cudaError_t e = cudaMemsetAsync(a.beam_max, 0, a.batch * sizeof(unsigned), s);
+    for (int sl = 0; sl < pl->p.n_slices && e == cudaSuccess; ++sl) {
+      a.trans = t + sl * plane;
+      e = launch_row_pass(n, sl == 0 ? ROW_BEAM0 : ROW_SLICE, a, s);
+      if (e == cudaSuccess) e = launch_col_pass(n, COL_SLICE, a, s);
+    }
+    if (e == cudaSuccess) e = launch_row_pass(n, ROW_IFFT_MAX, a, s);
+    if (e == cudaSuccess) e = launch_smatrix_store(a.wave, a.batch, n, b0, nb, a.beam_max, storage, L, smatrix, s);
+    if (e != cudaSuccess) return STEM_ERR_CUDA;
+  }
+  return STEM_OK;
+}
+
+// ----------------------------------------------------------------------------- PRISM output
+size_t stem_prism_output_workspace(stem_plan pl, int32_t f, int32_t chunk) {
+  if (!pl || !f_ok(pl, f) || chunk < 1) return 0;
+  const SmatLayout L = smatrix_layout(pl->n, pl->n_beams[log2i(f)], STEM_F32);
+  return output_workspace_layout(pl->n, f, chunk, L.nbp).total;
+}
+
+static stem_status output_common(stem_plan pl, int32_t f, stem_storage storage, int32_t engine, const void* smatrix,
+                                 OutputArgs& o) {
+  if (!pl || !smatrix || !f_ok(pl, f) || storage < STEM_F32 || storage > STEM_BF16) return STEM_ERR_INVALID;
+  if (engine < STEM_SUM_AUTO || engine > STEM_SUM_TENSOR) return STEM_ERR_INVALID;
+  if (pl->n < 64) return STEM_ERR_UNSUPPORTED;
+  const int lf = log2i(f);
+  const SmatLayout L = smatrix_layout(pl->n, pl->n_beams[lf], storage);
+  o.n = pl->n;
+  o.f = f;
+  o.w = pl->n / f;
+  o.storage = storage;
+  o.engine = engine == STEM_SUM_AUTO ? STEM_SUM_SIMT : engine;
+  if (o.engine == STEM_SUM_TENSOR) return STEM_ERR_UNSUPPORTED;
+  o.n_beams = L.n_beams;
+  o.nbp = L.nbp;
+  o.beams = pl->beams[lf];
+  o.smatrix = smatrix;
+  o.scales = static_cast<const float*>(smatrix);
+  o.sdata = static_cast<const char*>(smatrix) + L.data_offset;
+  o.lx = pl->p.cell[0];
+  o.ly = pl->p.cell[1];
+  o.dx = pl->p.cell[0] / pl->n;
+  o.dy = pl->p.cell[1] / pl->n;
+  o.coef_norm = (float)(1.0 / std::sqrt((double)std::max(L.n_beams, 1)));
+  return STEM_OK;
+}
+
+stem_status stem_prism_windows(stem_plan pl, int32_t f, stem_storage storage, int32_t engine, const void* smatrix,
+                               const double* probe_xy, int64_t n_probes, void* windows_out, void* ws, size_t ws_bytes,
+                               void* stream) {
+  OutputArgs o;
+  stem_status st = output_common(pl, f, storage, engine, smatrix, o);
+  if (st != STEM_OK) return st;
+  if (n_probes < 0 || n_probes > 65535 || (n_probes > 0 && (!probe_xy || !windows_out)) || !ws)
+    return STEM_ERR_INVALID;
+  if (n_probes == 0) return STEM_OK;
+  const OutputWs L = output_workspace_layout(o.n, f, (int)n_probes, o.nbp);
+  if (ws_bytes < L.total) return STEM_ERR_NOMEM;
+  return cuda_status(prism_windows_chunk(o, probe_xy, (int)n_probes, static_cast<float2*>(windows_out),
+                                         static_cast<char*>(ws), L, as_stream(stream)));
+}
+
+stem_status stem_prism_output(stem_plan pl, int32_t f, stem_storage storage, int32_t engine, const void* smatrix,
+                              const double* probe_xy, int64_t n_probes, int32_t chunk, float weight,
+                              float* rings_out, void* ws, size_t ws_bytes, void* stream) {
+  OutputArgs o;
+  stem_status st = output_common(pl, f, storage, engine, smatrix, o);
+  if (st != STEM_OK) return st;
+  if (n_probes < 0 || (n_probes > 0 && (!probe_xy || !rings_out)) || chunk < 1 || chunk > 65535 || !ws)
+    return STEM_ERR_INVALID;
+  const OutputWs L = output_workspace_layout(o.n, f, chunk, o.nbp);
+  if (ws_bytes < L.total) return STEM_ERR_NOMEM;
+  cudaStream_t s = as_stream(stream);
+  char* base = static_cast<char*>(ws);
+  float2* windows = reinterpret_cast<float2*>(base + L.windows);
+  const int lf = log2i(f);
+  const double w4 = std::pow((double)o.w, 4.0);
+  for (int64_t c0 = 0; c0 < n_probes; c0 += chunk) {
+    const int np = (int)std::min<int64_t>(chunk, n_probes - c0);
+    cudaError_t e = prism_windows_chunk(o, probe_xy + 2 * c0, np, windows, base, L, s);
+    PassArgs a;
+    a.wave = windows;
+    a.batch = np;
+    a.lut = pl->lut[lf];
+    a.n_rings = pl->p.n_rings;
+    a.rings = rings_out + c0 * pl->p.n_rings;
+    a.ring_scale = (float)(weight / w4);
+    if (e == cudaSuccess) e = launch_row_pass(o.w, ROW_FFT, a, s);
+    if (e == cudaSuccess) e = launch_col_pass(o.w, COL_DET, a, s);
+    if (e != cudaSuccess) return STEM_ERR_CUDA;
+  }
+  return STEM_OK;
+}
+
+// ----------------------------------------------------------------------------- detector, FFT
+stem_status stem_detector_readout(stem_plan pl, int32_t f, const void* psi_k, int64_t batch, float scale,
+                                  float* rings_out, void* stream) {
+  if (!pl || !f_ok(pl, f) || batch < 0 || batch > 65535 || (batch > 0 && (!psi_k || !rings_out)))
+    return STEM_ERR_INVALID;
+  return cuda_status(launch_readout(pl->n / f, static_cast<const float2*>(psi_k), batch, pl->lut[log2i(f)],
+                                    pl->p.n_rings, scale, rings_out, as_stream(stream)));
+}
+
+stem_status stem_fft2(int32_t n, int64_t batch, int32_t inverse, void* data, void* stream) {
+  if (!is_pow2(n) || n < 8 || n > 2048) return STEM_ERR_UNSUPPORTED;
+  if (batch < 0 || batch > 65535 || (batch > 0 && !data)) return STEM_ERR_INVALID;
+  PassArgs a;
+  a.wave = static_cast<float2*>(data);
+  a.batch = (int)batch;
+  cudaStream_t s = as_stream(stream);
+  cudaError_t e = launch_row_pass(n, inverse ? ROW_IFFT : ROW_FFT, a, s);
+  if (e == cudaSuccess) e = launch_col_pass(n, inverse ? COL_IFFT : COL_FFT, a, s);
+  return cuda_status(e);
+}
+
+// ----------------------------------------------------------------------------- footprint
+size_t stem_footprint_bytes(const stem_params* p, int32_t algo, int32_t f, stem_storage storage, int64_t n_probes,
+                            int32_t batch) {
+  if (check_params(p) != STEM_OK || batch < 1) return 0;
+  const size_t n = (size_t)p->n, plane = n * n;
+  const size_t trans = (size_t)p->n_slices * plane * sizeof(float2);
+  const size_t rings = (size_t)std::max<int64_t>(n_probes, 0) * p->n_rings * sizeof(float);
+  if (algo == 0) return trans + (size_t)batch * plane * sizeof(float2) + rings;
+  if (!is_pow2(f) || f > p->n / 8) return 0;
+  const int nb = count_beams(p, f, wavelength_a(p->energy_kev));
+  const SmatLayout L = smatrix_layout(p->n, nb, storage);
+  const int chunk = (int)std::min<int64_t>(std::max<int64_t>(n_probes, 1), 4096);
+  return trans + L.total + (size_t)batch * plane * sizeof(float2) + (size_t)batch * 4 +
+         output_workspace_layout(p->n, f, chunk, L.nbp).total + rings;
+}
+
+}  // extern "C"

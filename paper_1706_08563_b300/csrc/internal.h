@@ -1,0 +1,100 @@
+// internal.h - shared declarations of libstem's CUDA translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/stem.h"
+
+namespace stem {
+
+constexpr int kMaxLog2F = 11;      // f = 1 .. 2048
+constexpr int kMaxRings = 2048;
+constexpr uint16_t kLutNoRing = 0x7FFF;
+constexpr uint16_t kLutAperture = 0x8000;
+
+// Arguments of the fused row / column FFT passes.  Waves are [batch][N][N]
+// complex64, contiguous.
+struct PassArgs {
+  float2* wave = nullptr;
+  int batch = 0;
+  const float2* trans = nullptr;     // t_n [N][N] of the current slice (row passes)
+  const float2* prop_x = nullptr;    // exp(-i pi lambda dz (m/Lx)^2), [N]
+  const float2* prop_y = nullptr;    // exp(-i pi lambda dz (n/Ly)^2), [N]
+  float prop_scale = 1.0f;           // 1/N^2 folds the inverse-FFT normalisation in
+  const uint16_t* lut = nullptr;     // [N][N]: bit 15 aperture, bits 0..14 ring or 0x7FFF
+  int n_rings = 0;
+  float* rings = nullptr;            // [batch][n_rings] (offset to the batch's first wave)
+  float ring_scale = 1.0f;
+  const double* probe_xy = nullptr;  // [batch][2] (offset)
+  double inv_lx = 0.0, inv_ly = 0.0;
+  float probe_norm = 0.0f;           // 1 / (sqrt(|A|) N^2)
+  const int2* beams = nullptr;       // [batch] (m, n) (offset)
+  unsigned* beam_max = nullptr;      // [batch] float bits of max(|Re|, |Im|)
+};
+
+enum RowMode { ROW_SLICE = 0, ROW_BEAM0 = 1, ROW_IFFT_MAX = 2, ROW_FFT = 3, ROW_IFFT = 4 };
+enum ColMode { COL_SLICE = 0, COL_DET = 1, COL_PROBE_INIT = 2, COL_FFT = 3, COL_IFFT = 4 };
+
+cudaError_t launch_row_pass(int n, int mode, const PassArgs& a, cudaStream_t s);
+cudaError_t launch_col_pass(int n, int mode, const PassArgs& a, cudaStream_t s);
+
+// Potentials (potential.cu)
+size_t potential_workspace(int64_t n_atoms);
+cudaError_t launch_potentials(const stem_params& p, double sigma, const double* xyz, const float* gauss,
+                              int64_t n_atoms, float* v_out, float2* t_out, void* ws, cudaStream_t s);
+
+// PRISM helpers (prism.cu)
+struct SmatLayout {
+  int n_beams = 0;
+  int nbp = 0;            // beams padded to 64
+  size_t data_offset = 0; // bytes
+  size_t elem_bytes = 4;
+  size_t total = 0;
+};
+SmatLayout smatrix_layout(int n, int n_beams, int storage);
+
+cudaError_t launch_smatrix_store(const float2* waves, int nb, int n, int b0, int n_beams_total,
+                                 const unsigned* beam_max, int storage, const SmatLayout& L,
+                                 void* smatrix, cudaStream_t s);
+
+struct OutputWs {
+  size_t coef = 0, origin = 0, counts = 0, offsets = 0, work = 0, list = 0, windows = 0, total = 0;
+};
+OutputWs output_workspace_layout(int n, int f, int chunk, int nbp);
+
+struct OutputArgs {
+  int n = 0, f = 0, w = 0, storage = 0, engine = 0;
+  int n_beams = 0, nbp = 0;
+  const int2* beams = nullptr;
+  const void* smatrix = nullptr;
+  const float* scales = nullptr;
+  const void* sdata = nullptr;
+  double lx = 0, ly = 0, dx = 0, dy = 0;
+  float coef_norm = 0.0f;
+};
+cudaError_t prism_windows_chunk(const OutputArgs& o, const double* probe_xy, int np, float2* windows,
+                                char* ws, const OutputWs& L, cudaStream_t s);
+
+// detector readout on a standalone k-space batch (detector.cu)
+cudaError_t launch_readout(int w, const float2* psi_k, int64_t batch, const uint16_t* lut, int n_rings,
+                           float scale, float* rings, cudaStream_t s);
+
+}  // namespace stem
+
+// Plan object (library-owned device tables).
+struct stem_plan_s {
+  stem_params p{};
+  double lam = 0.0, sigma = 0.0;
+  int n = 0;
+  int n_aperture = 0;
+  int device = 0;
+  float2* prop_x = nullptr;
+  float2* prop_y = nullptr;
+  uint16_t* lut[stem::kMaxLog2F + 1] = {};
+  int2* beams[stem::kMaxLog2F + 1] = {};
+  int n_beams[stem::kMaxLog2F + 1] = {};
+  std::vector<int2> h_beams[stem::kMaxLog2F + 1];
+};

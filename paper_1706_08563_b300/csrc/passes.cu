@@ -1,0 +1,290 @@
+// passes.cu - fused row / column FFT passes of the multislice slice loop.
+//
+// One slice (Eq. 1 then Eq. 2) of a batch of waves is two passes over HBM:
+//   row pass:    [row IFFT] -> x t_n (Eq. 1) -> row FFT
+//   column pass: col FFT -> x M P / N^2 (Eq. 2, 2/3 band limit) -> col IFFT
+// so the wave is read and written twice per slice (32 bytes per pixel).  The
+// first row pass of a probe follows the column pass that builds the probe
+// (Fourier-space aperture and phase ramp, then a column IFFT); the last column
+// pass of multislice squares |FFT| and bins it into rings instead of storing
+// (|P| = 1, so the last propagator phase does not change intensities).
+#include <mutex>
+
+#include "fft_core.cuh"
+#include "internal.h"
+
+namespace stem {
+
+template <int N> struct RowCfg {
+  static constexpr int E = FftShape<N>::E;
+  static constexpr int T = N / E;
+  static constexpr int ROWS = (256 / T) < N ? (256 / T) : N;
+  static constexpr int THREADS = ROWS * T;
+  static constexpr int ROWBUF = N + N / E;
+  static constexpr size_t SMEM = (size_t)ROWS * ROWBUF * sizeof(float2);
+};
+
+template <int N> struct ColCfg {
+  static constexpr int E = FftShape<N>::E;
+  static constexpr int T = N / E;
+  static constexpr int C0 = (256 / T) > 16 ? 16 : (256 / T);
+  static constexpr int C = C0 < 1 ? 1 : (C0 > N ? N : C0);
+  static constexpr int THREADS = C * T;
+  static constexpr size_t FFT_SMEM = (size_t)(N + N / E) * C * sizeof(float2);
+};
+
+__device__ __forceinline__ int signed_freq(int j, int n) { return j < (n >> 1) ? j : j - n; }
+
+// ---------------------------------------------------------------------------
+// Row pass: CTA = (wave, tile of ROWS rows).  blockIdx.x runs over the waves so
+// that consecutive CTAs read the same rows of t_n (kept in L2 for the batch).
+// ---------------------------------------------------------------------------
+template <int N, int MODE>
+__global__ void __launch_bounds__(RowCfg<N>::THREADS) k_row_pass(const PassArgs a) {
+  using Cfg = RowCfg<N>;
+  constexpr int E = Cfg::E, T = Cfg::T;
+  extern __shared__ float2 smem[];
+  const int t = threadIdx.x % T;
+  const int rl = threadIdx.x / T;
+  const int wave = blockIdx.x;
+  const int row = blockIdx.y * Cfg::ROWS + rl;
+  float2* w = a.wave + (size_t)wave * N * N + (size_t)row * N;
+  const SmemView<E, 1> view{smem + rl * Cfg::ROWBUF};
+  auto sync = [] {
+    if constexpr (T > 32 || Cfg::THREADS <= 32) __syncthreads();
+    else __syncwarp();
+  };
+
+  float2 v[E];
+  if constexpr (MODE == ROW_BEAM0) {
+    // plane wave exp(2 pi i (m x + n y) / N), argument reduced exactly in integers
+    const int2 mn = a.beams[wave];
+#pragma unroll
+    for (int q = 0; q < E; ++q) {
+      const int x = t + q * T;
+      const int k = (int)((((long long)mn.x * x + (long long)mn.y * row) % N + N) % N);
+      float s, c;
+      sincospif(2.0f * (float)k / (float)N, &s, &c);
+      v[q] = make_float2(c, s);
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < E; ++q) v[q] = w[t + q * T];
+  }
+
+  if constexpr (MODE == ROW_SLICE || MODE == ROW_IFFT_MAX || MODE == ROW_IFFT)
+    fft_dist<N, true>(v, view, t, sync);
+
+  if constexpr (MODE == ROW_SLICE || MODE == ROW_BEAM0) {
+    const float2* tr = a.trans + (size_t)row * N;
+#pragma unroll
+    for (int q = 0; q < E; ++q) v[q] = cmul(v[q], __ldg(tr + t + q * T));
+  }
+
+  if constexpr (MODE == ROW_SLICE || MODE == ROW_BEAM0 || MODE == ROW_FFT)
+    fft_dist<N, false>(v, view, t, sync);
+
+#pragma unroll
+  for (int q = 0; q < E; ++q) w[t + q * T] = v[q];
+
+  if constexpr (MODE == ROW_IFFT_MAX) {
+    float m = 0.0f;
+#pragma unroll
+    for (int q = 0; q < E; ++q) m = fmaxf(m, fmaxf(fabsf(v[q].x), fabsf(v[q].y)));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(a.beam_max + wave, __float_as_uint(m));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Column pass: CTA = (tile of C columns, wave).  Thread (c, t) = threadIdx
+// c + C t holds column elements t + T q; neighbouring lanes read neighbouring
+// columns, so every global access is C * 8 contiguous bytes.
+// ---------------------------------------------------------------------------
+template <int N, int MODE>
+__global__ void __launch_bounds__(ColCfg<N>::THREADS) k_col_pass(const PassArgs a) {
+  using Cfg = ColCfg<N>;
+  constexpr int E = Cfg::E, T = Cfg::T, C = Cfg::C;
+  extern __shared__ float2 smem[];
+  const int c = threadIdx.x % C;
+  const int t = threadIdx.x / C;
+  const int col = blockIdx.x * C + c;
+  const int wave = blockIdx.y;
+  float2* w = a.wave + (size_t)wave * N * N + col;
+  const SmemView<E, C> view{smem + c};
+  auto sync = [] { __syncthreads(); };
+  float* ring_acc = reinterpret_cast<float*>(smem + (N + N / E) * C);
+
+  if constexpr (MODE == COL_DET) {
+    for (int i = threadIdx.x; i < a.n_rings; i += Cfg::THREADS) ring_acc[i] = 0.0f;
+  }
+
+  float2 v[E];
+  if constexpr (MODE == COL_PROBE_INIT) {
+    // psi_hat(m, n) = A(m, n) exp(-2 pi i (m x_p / Lx + n y_p / Ly)) / (sqrt|A| N^2);
+    // the phase is reduced in FP64, then evaluated in FP32.
+    const double xp = a.probe_xy[2 * wave], yp = a.probe_xy[2 * wave + 1];
+    const double thx = (double)signed_freq(col, N) * xp * a.inv_lx;
+#pragma unroll
+    for (int q = 0; q < E; ++q) {
+      const int ky = t + q * T;
+      const uint16_t l = __ldg(a.lut + (size_t)ky * N + col);
+      float2 val = make_float2(0.0f, 0.0f);
+      if (l & kLutAperture) {
+        double th = thx + (double)signed_freq(ky, N) * yp * a.inv_ly;
+        th -= rint(th);
+        float s, cth;
+        sincospif(-2.0f * (float)th, &s, &cth);
+        val = make_float2(cth * a.probe_norm, s * a.probe_norm);
+      }
+      v[q] = val;
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < E; ++q) v[q] = w[(size_t)(t + q * T) * N];
+  }
+
+  if constexpr (MODE == COL_SLICE || MODE == COL_DET || MODE == COL_FFT)
+    fft_dist<N, false>(v, view, t, sync);
+
+  if constexpr (MODE == COL_SLICE) {
+    const int m = signed_freq(col, N);
+    const float2 px = cscale(__ldg(a.prop_x + col), a.prop_scale);
+#pragma unroll
+    for (int q = 0; q < E; ++q) {
+      const int ky = t + q * T;
+      const int n = signed_freq(ky, N);
+      const bool keep = 9 * (m * m + n * n) <= N * N;
+      v[q] = keep ? cmul(v[q], cmul(px, __ldg(a.prop_y + ky))) : make_float2(0.0f, 0.0f);
+    }
+  }
+
+  if constexpr (MODE == COL_SLICE || MODE == COL_PROBE_INIT || MODE == COL_IFFT)
+    fft_dist<N, true>(v, view, t, sync);
+
+  if constexpr (MODE == COL_DET) {
+    __syncthreads();   // ring_acc zeroed
+#pragma unroll
+    for (int q = 0; q < E; ++q) {
+      const int ky = t + q * T;
+      const int r = __ldg(a.lut + (size_t)ky * N + col) & kLutNoRing;
+      if (r != kLutNoRing) atomicAdd(ring_acc + r, cabs2(v[q]));
+    }
+    __syncthreads();
+    float* out = a.rings + (size_t)wave * a.n_rings;
+    for (int i = threadIdx.x; i < a.n_rings; i += Cfg::THREADS) {
+      const float acc = ring_acc[i];
+      if (acc != 0.0f) atomicAdd(out + i, acc * a.ring_scale);
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < E; ++q) w[(size_t)(t + q * T) * N] = v[q];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Launchers.  The dynamic shared-memory opt-in is set once per kernel in this
+// process (the library drives the device that was current at plan creation).
+// ---------------------------------------------------------------------------
+template <class K>
+static cudaError_t set_smem(K kernel, size_t bytes, std::once_flag& flag) {
+  cudaError_t err = cudaSuccess;
+  std::call_once(flag, [&] {
+    err = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  });
+  return err;
+}
+
+template <int N, int MODE>
+static cudaError_t row_launch(const PassArgs& a, cudaStream_t s) {
+  using Cfg = RowCfg<N>;
+  static std::once_flag flag;
+  cudaError_t e = set_smem(k_row_pass<N, MODE>, Cfg::SMEM, flag);
+  if (e != cudaSuccess) return e;
+  dim3 grid(a.batch, N / Cfg::ROWS);
+  k_row_pass<N, MODE><<<grid, Cfg::THREADS, Cfg::SMEM, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int N, int MODE>
+static cudaError_t col_launch(const PassArgs& a, cudaStream_t s) {
+  using Cfg = ColCfg<N>;
+  const size_t smem = Cfg::FFT_SMEM + (MODE == COL_DET ? kMaxRings * sizeof(float) : 0);
+  static std::once_flag flag;
+  cudaError_t e = set_smem(k_col_pass<N, MODE>, Cfg::FFT_SMEM + kMaxRings * sizeof(float), flag);
+  if (e != cudaSuccess) return e;
+  dim3 grid(N / Cfg::C, a.batch);
+  k_col_pass<N, MODE><<<grid, Cfg::THREADS, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int N>
+static cudaError_t row_dispatch(int mode, const PassArgs& a, cudaStream_t s) {
+  switch (mode) {
+    case ROW_FFT: return row_launch<N, ROW_FFT>(a, s);
+    case ROW_IFFT: return row_launch<N, ROW_IFFT>(a, s);
+    default: break;
+  }
+  if constexpr (N >= 64) {
+    switch (mode) {
+      case ROW_SLICE: return row_launch<N, ROW_SLICE>(a, s);
+      case ROW_BEAM0: return row_launch<N, ROW_BEAM0>(a, s);
+      case ROW_IFFT_MAX: return row_launch<N, ROW_IFFT_MAX>(a, s);
+      default: break;
+    }
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <int N>
+static cudaError_t col_dispatch(int mode, const PassArgs& a, cudaStream_t s) {
+  switch (mode) {
+    case COL_DET: return col_launch<N, COL_DET>(a, s);
+    case COL_FFT: return col_launch<N, COL_FFT>(a, s);
+    case COL_IFFT: return col_launch<N, COL_IFFT>(a, s);
+    default: break;
+  }
+  if constexpr (N >= 64) {
+    switch (mode) {
+      case COL_SLICE: return col_launch<N, COL_SLICE>(a, s);
+      case COL_PROBE_INIT: return col_launch<N, COL_PROBE_INIT>(a, s);
+      default: break;
+    }
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_row_pass(int n, int mode, const PassArgs& a, cudaStream_t s) {
+  if (a.batch <= 0) return cudaSuccess;
+  switch (n) {
+    case 8: return row_dispatch<8>(mode, a, s);
+    case 16: return row_dispatch<16>(mode, a, s);
+    case 32: return row_dispatch<32>(mode, a, s);
+    case 64: return row_dispatch<64>(mode, a, s);
+    case 128: return row_dispatch<128>(mode, a, s);
+    case 256: return row_dispatch<256>(mode, a, s);
+    case 512: return row_dispatch<512>(mode, a, s);
+    case 1024: return row_dispatch<1024>(mode, a, s);
+    case 2048: return row_dispatch<2048>(mode, a, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_col_pass(int n, int mode, const PassArgs& a, cudaStream_t s) {
+  if (a.batch <= 0) return cudaSuccess;
+  switch (n) {
+    case 8: return col_dispatch<8>(mode, a, s);
+    case 16: return col_dispatch<16>(mode, a, s);
+    case 32: return col_dispatch<32>(mode, a, s);
+    case 64: return col_dispatch<64>(mode, a, s);
+    case 128: return col_dispatch<128>(mode, a, s);
+    case 256: return col_dispatch<256>(mode, a, s);
+    case 512: return col_dispatch<512>(mode, a, s);
+    case 1024: return col_dispatch<1024>(mode, a, s);
+    case 2048: return col_dispatch<2048>(mode, a, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace stem

@@ -1,0 +1,242 @@
+"""PyTorch-facing binding of libstem (argument marshalling only).
+
+Every computation runs in libstem's CUDA kernels; this module checks tensor
+devices, dtypes and shapes, allocates outputs and workspaces with PyTorch (the
+device-memory provider) and passes raw pointers plus the current CUDA stream
+through the C ABI.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+from typing import Optional, Tuple
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import ENGINE, STORAGE, StemParams, check
+
+
+def _stream(device: torch.device) -> ctypes.c_void_p:
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _ptr(t: Optional[torch.Tensor]) -> ctypes.c_void_p:
+    return ctypes.c_void_p(0 if t is None else t.data_ptr())
+
+
+def _need(t: torch.Tensor, dtype: torch.dtype, name: str, shape=None) -> torch.Tensor:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    return t.contiguous()
+
+
+def _workspace(nbytes: int, device) -> torch.Tensor:
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+
+
+@dataclass
+class SMatrix:
+    """A compact S-matrix buffer filled by ``Plan.prism_smatrix``."""
+    buf: torch.Tensor          # uint8, stem_prism_smatrix_bytes
+    f: int
+    storage: str
+    n_beams: int
+    nbp: int
+    data_offset: int
+    n: int
+
+    def scales(self) -> torch.Tensor:
+        return self.buf[: 4 * self.nbp].view(torch.float32)
+
+    def data(self) -> torch.Tensor:
+        """[n, n, 2, nbp] view of the stored values (S_b / s_b)."""
+        dt = {"f32": torch.float32, "f16": torch.float16, "bf16": torch.bfloat16}[self.storage]
+        esz = 4 if self.storage == "f32" else 2
+        raw = self.buf[self.data_offset: self.data_offset + self.n * self.n * 2 * self.nbp * esz]
+        return raw.view(dt).view(self.n, self.n, 2, self.nbp)
+
+    def beams_real_space(self) -> torch.Tensor:
+        """S_b(y, x) as complex64 [n_beams, n, n] (scaled back)."""
+        d = self.data().float() * self.scales()[None, None, None, :]
+        c = torch.complex(d[:, :, 0, :], d[:, :, 1, :])
+        return c.permute(2, 0, 1)[: self.n_beams].contiguous()
+
+
+class Plan:
+    """A stem_plan: grid, optics and detector tables on the current CUDA device."""
+
+    def __init__(self, cell, n, n_slices, slice_dz, energy_kev, alpha_mrad, ring_width_mrad, n_rings,
+                 device=None):
+        lib = _lib.load()
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else
+                                   torch.device(device).index or 0)
+        self.params = StemParams((ctypes.c_double * 3)(*[float(c) for c in cell]), int(n), int(n_slices),
+                                 float(slice_dz), float(energy_kev), float(alpha_mrad),
+                                 float(ring_width_mrad), int(n_rings))
+        handle = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            check(lib.stem_plan_create(ctypes.byref(self.params), ctypes.byref(handle)), "stem_plan_create")
+        self._h = handle
+        self.n = int(n)
+        self.n_slices = int(n_slices)
+        self.n_rings = int(n_rings)
+        lam, sig, nap = ctypes.c_double(), ctypes.c_double(), ctypes.c_int32()
+        check(lib.stem_plan_constants(self._h, ctypes.byref(lam), ctypes.byref(sig), ctypes.byref(nap)),
+              "stem_plan_constants")
+        self.lam, self.sigma, self.n_aperture = lam.value, sig.value, nap.value
+
+    @classmethod
+    def from_workload(cls, w, device=None) -> "Plan":
+        return cls(w.cell, w.n, w.n_slices, w.slice_dz, w.energy_kev, w.alpha_mrad, w.ring_width_mrad,
+                   w.n_rings, device=device)
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            _lib.load().stem_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------------ potentials
+    def slice_potentials(self, xyz: torch.Tensor, gauss: torch.Tensor, want_v: bool = False):
+        """t_n = exp(i sigma V_n) as complex64 [S, N, N] (and V_n float32 if want_v)."""
+        lib = _lib.load()
+        xyz = _need(xyz, torch.float64, "xyz")
+        gauss = _need(gauss, torch.float32, "gauss")
+        na = xyz.shape[0]
+        if xyz.shape != (na, 3) or gauss.shape != (na, 4):
+            raise ValueError("xyz must be [n,3] and gauss [n,4]")
+        trans = torch.empty((self.n_slices, self.n, self.n), dtype=torch.complex64, device=self.device)
+        v = torch.empty((self.n_slices, self.n, self.n), dtype=torch.float32, device=self.device) if want_v else None
+        nws = lib.stem_slice_potentials_workspace(self._h, na)
+        ws = _workspace(nws, self.device)
+        check(lib.stem_slice_potentials(self._h, _ptr(xyz), _ptr(gauss), na, _ptr(v), _ptr(trans), _ptr(ws),
+                                        ws.numel(), _stream(self.device)), "stem_slice_potentials")
+        return (trans, v) if want_v else trans
+
+    # ------------------------------------------------------------------ multislice
+    def multislice_workspace(self, batch: int) -> torch.Tensor:
+        return _workspace(_lib.load().stem_multislice_workspace(self._h, batch), self.device)
+
+    def multislice(self, trans: torch.Tensor, probe_xy: torch.Tensor, batch: int = 256,
+                   rings: Optional[torch.Tensor] = None, weight: float = 1.0,
+                   workspace: Optional[torch.Tensor] = None) -> torch.Tensor:
+        lib = _lib.load()
+        trans = _need(trans, torch.complex64, "trans", (self.n_slices, self.n, self.n))
+        probe_xy = _need(probe_xy, torch.float64, "probe_xy")
+        npr = probe_xy.shape[0]
+        if rings is None:
+            rings = torch.zeros((npr, self.n_rings), dtype=torch.float32, device=self.device)
+        else:
+            rings = _need(rings, torch.float32, "rings", (npr, self.n_rings))
+        batch = int(max(1, min(batch, max(npr, 1))))
+        ws = workspace if workspace is not None else self.multislice_workspace(batch)
+        check(lib.stem_multislice_scan(self._h, _ptr(trans), _ptr(probe_xy), npr, batch, float(weight),
+                                       _ptr(rings), _ptr(ws), ws.numel(), _stream(self.device)),
+              "stem_multislice_scan")
+        return rings
+
+    # ------------------------------------------------------------------ PRISM
+    def prism_beams(self, f: int) -> np.ndarray:
+        lib = _lib.load()
+        nb = ctypes.c_int32()
+        check(lib.stem_prism_beams(self._h, f, ctypes.byref(nb), None), "stem_prism_beams")
+        out = np.zeros((nb.value, 2), dtype=np.int32)
+        check(lib.stem_prism_beams(self._h, f, ctypes.byref(nb), out.ctypes.data_as(ctypes.c_void_p)),
+              "stem_prism_beams")
+        return out
+
+    def prism_smatrix(self, trans: torch.Tensor, f: int, storage: str = "f32", batch: int = 128,
+                      workspace: Optional[torch.Tensor] = None, out: Optional[torch.Tensor] = None) -> SMatrix:
+        lib = _lib.load()
+        trans = _need(trans, torch.complex64, "trans", (self.n_slices, self.n, self.n))
+        st = STORAGE[storage]
+        nbytes = lib.stem_prism_smatrix_bytes(self._h, f, st)
+        if nbytes == 0:
+            raise ValueError(f"unsupported f={f} or storage={storage}")
+        nb = len(self.prism_beams(f))
+        batch = int(max(1, min(batch, nb)))
+        buf = out if out is not None else torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        ws = workspace if workspace is not None else _workspace(
+            lib.stem_prism_smatrix_workspace(self._h, batch), self.device)
+        check(lib.stem_prism_smatrix(self._h, _ptr(trans), f, st, batch, _ptr(buf), buf.numel(), _ptr(ws),
+                                     ws.numel(), _stream(self.device)), "stem_prism_smatrix")
+        nbp = (nb + 63) // 64 * 64
+        return SMatrix(buf, f, storage, nb, nbp, (nbp * 4 + 255) // 256 * 256, self.n)
+
+    def prism_output_workspace(self, f: int, chunk: int) -> torch.Tensor:
+        return _workspace(_lib.load().stem_prism_output_workspace(self._h, f, chunk), self.device)
+
+    def prism_output(self, smat: SMatrix, probe_xy: torch.Tensor, chunk: int = 4096, engine: str = "auto",
+                     rings: Optional[torch.Tensor] = None, weight: float = 1.0,
+                     workspace: Optional[torch.Tensor] = None) -> torch.Tensor:
+        lib = _lib.load()
+        probe_xy = _need(probe_xy, torch.float64, "probe_xy")
+        npr = probe_xy.shape[0]
+        if rings is None:
+            rings = torch.zeros((npr, self.n_rings), dtype=torch.float32, device=self.device)
+        else:
+            rings = _need(rings, torch.float32, "rings", (npr, self.n_rings))
+        chunk = int(max(1, min(chunk, max(npr, 1), 65535)))
+        ws = workspace if workspace is not None else self.prism_output_workspace(smat.f, chunk)
+        check(lib.stem_prism_output(self._h, smat.f, STORAGE[smat.storage], ENGINE[engine], _ptr(smat.buf),
+                                    _ptr(probe_xy), npr, chunk, float(weight), _ptr(rings), _ptr(ws), ws.numel(),
+                                    _stream(self.device)), "stem_prism_output")
+        return rings
+
+    def prism_windows(self, smat: SMatrix, probe_xy: torch.Tensor, engine: str = "auto") -> torch.Tensor:
+        lib = _lib.load()
+        probe_xy = _need(probe_xy, torch.float64, "probe_xy")
+        npr = probe_xy.shape[0]
+        w = self.n // smat.f
+        out = torch.empty((npr, w, w), dtype=torch.complex64, device=self.device)
+        ws = self.prism_output_workspace(smat.f, max(npr, 1))
+        check(lib.stem_prism_windows(self._h, smat.f, STORAGE[smat.storage], ENGINE[engine], _ptr(smat.buf),
+                                     _ptr(probe_xy), npr, _ptr(out), _ptr(ws), ws.numel(), _stream(self.device)),
+              "stem_prism_windows")
+        return out
+
+    # ------------------------------------------------------------------ detector
+    def detector_readout(self, psi_k: torch.Tensor, f: int = 1, scale: float = 1.0,
+                         rings: Optional[torch.Tensor] = None) -> torch.Tensor:
+        lib = _lib.load()
+        w = self.n // f
+        psi_k = _need(psi_k, torch.complex64, "psi_k")
+        if psi_k.dim() != 3 or psi_k.shape[1:] != (w, w):
+            raise ValueError(f"psi_k must be [batch, {w}, {w}]")
+        b = psi_k.shape[0]
+        if rings is None:
+            rings = torch.zeros((b, self.n_rings), dtype=torch.float32, device=self.device)
+        check(lib.stem_detector_readout(self._h, f, _ptr(psi_k), b, float(scale), _ptr(rings), _stream(self.device)),
+              "stem_detector_readout")
+        return rings
+
+
+def fft2(x: torch.Tensor, inverse: bool = False) -> torch.Tensor:
+    """Batched 2D FFT of complex64 [batch, n, n] with libstem's kernels (unnormalised)."""
+    lib = _lib.load()
+    x = _need(x, torch.complex64, "x").clone()
+    if x.dim() != 3 or x.shape[1] != x.shape[2]:
+        raise ValueError("x must be [batch, n, n]")
+    check(lib.stem_fft2(x.shape[1], x.shape[0], 1 if inverse else 0, _ptr(x), _stream(x.device)), "stem_fft2")
+    return x
+
+
+def footprint_bytes(w, algo: str = "ms", f: int = 1, storage: str = "f32", batch: int = 256) -> int:
+    """Device bytes a simulation of workload ``w`` needs (admission control)."""
+    lib = _lib.load()
+    p = StemParams((ctypes.c_double * 3)(*[float(c) for c in w.cell]), int(w.n), int(w.n_slices),
+                   float(w.slice_dz), float(w.energy_kev), float(w.alpha_mrad), float(w.ring_width_mrad),
+                   int(w.n_rings))
+    return int(lib.stem_footprint_bytes(ctypes.byref(p), 0 if algo == "ms" else 1, f, STORAGE[storage],
+                                        w.n_probes, batch))

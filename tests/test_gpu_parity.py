@@ -1,0 +1,270 @@
+"""CUDA path (through the C ABI) vs the FP64 oracle, element by element.
+
+Tolerances: FP32 arithmetic is held to relative L2 <= 1e-4 on every ring image
+(the whole [probe, ring] array and each ring whose reference norm is above
+1e-6 of the largest); FP16/BF16 S-matrix storage to <= 1e-2; unit kernels
+(FFT, potentials) to their FP32 rounding level.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+from oracle import stem as O
+
+pytestmark = pytest.mark.gpu
+
+FP32_TOL = 1e-4
+LOWP_TOL = 1e-2
+
+
+def rel_l2(a, b):
+    return O.rel_l2(np.asarray(a, np.float64), np.asarray(b, np.float64))
+
+
+def check_rings(got, ref, tol):
+    got = np.asarray(got, np.float64)
+    ref = np.asarray(ref, np.float64)
+    assert got.shape == ref.shape
+    assert rel_l2(got, ref) <= tol, rel_l2(got, ref)
+    norms = np.sqrt(np.mean(ref ** 2, axis=0))
+    for i in np.nonzero(norms >= 1e-6 * norms.max())[0]:
+        e = rel_l2(got[:, i], ref[:, i])
+        assert e <= tol, (i, e)
+
+
+@pytest.fixture(scope="module")
+def api():
+    from paper_1706_08563_b300 import api as A
+    return A
+
+
+def dev(x, dtype=None):
+    t = torch.as_tensor(np.ascontiguousarray(x))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.cuda()
+
+
+# ------------------------------------------------------------------------ FFT
+@pytest.mark.parametrize("n,batch", [(8, 3), (16, 5), (32, 3), (64, 7), (128, 3), (256, 2), (512, 2),
+                                     (1024, 2), (2048, 1)])
+@pytest.mark.parametrize("inverse", [False, True])
+def test_fft2_vs_numpy(api, n, batch, inverse):
+    x = W.random_complex((batch, n, n), seed=n + batch)
+    got = api.fft2(dev(x, torch.complex64), inverse=inverse).cpu().numpy()
+    ref = np.fft.ifft2(x) * n * n if inverse else np.fft.fft2(x)
+    err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    assert err <= 1e-6, err
+
+
+# ---------------------------------------------------------------- potentials
+def test_potentials_vs_oracle(api):
+    w = W.scaled(W.C1, n_atoms=60)
+    xyz, gauss = W.atoms(w, seed=11)
+    xyz[0] = [0.01, 15.99, 0.5]            # periodic images along both axes
+    xyz[1] = [8.0, 8.0, 19.999]            # last slice
+    plan = api.Plan.from_workload(w)
+    trans, v = plan.slice_potentials(dev(xyz), dev(gauss), want_v=True)
+    p = O.params_from(w)
+    vref = O.projected_potential(p, xyz, gauss)
+    v = v.cpu().numpy()
+    assert np.max(np.abs(v - vref)) <= 2e-6 * np.max(vref)
+    tref = O.transmission(p, vref)
+    assert np.max(np.abs(trans.cpu().numpy() - tref)) <= 2e-6
+
+
+# ------------------------------------------------------------------ detector
+def test_detector_readout_vs_oracle(api):
+    w = W.scaled(W.C1, n=64)
+    plan = api.Plan.from_workload(w)
+    p = O.params_from(w)
+    for f in (1, 2, 4):
+        x = W.random_complex((5, 64 // f, 64 // f), seed=f)
+        got = plan.detector_readout(dev(x, torch.complex64), f=f, scale=0.5).cpu().numpy()
+        table = O.ring_table(p) if f == 1 else O.coarse_ring_table(p, f)
+        ref = 0.5 * O.detector_rings(table, p.n_rings, np.abs(x) ** 2)
+        assert np.max(np.abs(got - ref)) <= 1e-5 * np.max(ref)
+
+
+# ---------------------------------------------------------------- multislice
+def _oracle_trans(w, xyz, gauss):
+    p = O.params_from(w)
+    return p, O.transmission(p, O.projected_potential(p, xyz, gauss))
+
+
+def test_multislice_c1_end_to_end(api):
+    """Config 1 in full: 200 atoms, 128^2, 10 slices, 80 keV, 16x16 probes."""
+    w = W.C1
+    xyz, gauss = W.atoms(w)
+    xy = W.scan_positions(w)
+    plan = api.Plan.from_workload(w)
+    trans = plan.slice_potentials(dev(xyz), dev(gauss))
+    got = plan.multislice(trans, dev(xy), batch=w.batch).cpu().numpy()
+    p, tref = _oracle_trans(w, xyz, gauss)
+    ref = O.multislice_rings(p, tref, xy, chunk=64)
+    check_rings(got, ref, FP32_TOL)
+    # stage-wise: the same oracle transmission on both sides isolates propagation
+    got2 = plan.multislice(dev(tref, torch.complex64), dev(xy), batch=w.batch).cpu().numpy()
+    check_rings(got2, ref, FP32_TOL)
+
+
+def test_multislice_ragged_batches_and_weight(api):
+    """37 probes in launches of 16 (a ragged tail), N = 64, accumulation with weight."""
+    w = W.scaled(W.C1, n=64, n_atoms=40, n_slices=4, slice_dz=5.0)
+    xyz, gauss = W.atoms(w, seed=3)
+    xy = W.random_positions(w, 37, seed=4)
+    plan = api.Plan.from_workload(w)
+    p, tref = _oracle_trans(w, xyz, gauss)
+    t = dev(tref, torch.complex64)
+    rings = torch.full((37, w.n_rings), 0.25, dtype=torch.float32, device="cuda")
+    plan.multislice(t, dev(xy), batch=16, rings=rings, weight=0.5)
+    ref = O.multislice_rings(p, tref, xy)
+    check_rings(rings.cpu().numpy() - 0.25, 0.5 * ref, FP32_TOL)
+    one = plan.multislice(t, dev(xy), batch=37).cpu().numpy()
+    many = plan.multislice(t, dev(xy), batch=1).cpu().numpy()
+    check_rings(one, ref, FP32_TOL)
+    check_rings(many, ref, FP32_TOL)
+
+
+@pytest.mark.parametrize("n", [64, 256, 512])
+def test_multislice_sizes(api, n):
+    w = W.Workload("t", (20.0, 24.0, 8.0), 30, n, 4, 2.0, 200.0, 25.0, 3, 2.0, 60)
+    xyz, gauss = W.atoms(w, seed=n)
+    xy = W.random_positions(w, 5, seed=n + 1)
+    plan = api.Plan.from_workload(w)
+    p, tref = _oracle_trans(w, xyz, gauss)
+    got = plan.multislice(dev(tref, torch.complex64), dev(xy), batch=4).cpu().numpy()
+    check_rings(got, O.multislice_rings(p, tref, xy), FP32_TOL)
+
+
+def test_multislice_free_space_closed_form(api):
+    """V = 0: rings equal |A cap ring| / |A| at every probe position."""
+    w = W.scaled(W.C1, n=128)
+    plan = api.Plan.from_workload(w)
+    p = O.params_from(w)
+    t = torch.ones((w.n_slices, 128, 128), dtype=torch.complex64, device="cuda")
+    xy = W.random_positions(w, 9, seed=2)
+    got = plan.multislice(t, dev(xy), batch=9).cpu().numpy()
+    ap = O.aperture(p)
+    tab = O.ring_table(p)
+    want = np.array([np.sum(ap & (tab == i)) for i in range(p.n_rings)]) / ap.sum()
+    assert np.max(np.abs(got - want[None])) <= 1e-5
+
+
+def test_multislice_empty_and_errors(api):
+    from paper_1706_08563_b300 import _lib
+    w = W.scaled(W.C1, n=64, n_slices=2)
+    plan = api.Plan.from_workload(w)
+    t = torch.ones((2, 64, 64), dtype=torch.complex64, device="cuda")
+    r = plan.multislice(t, torch.zeros((0, 2), dtype=torch.float64, device="cuda"))
+    assert r.shape == (0, w.n_rings)
+    lib = _lib.load()
+    ws = plan.multislice_workspace(4)
+    xy = torch.zeros((4, 2), dtype=torch.float64, device="cuda")
+    rings = torch.zeros((4, w.n_rings), device="cuda")
+    assert lib.stem_multislice_scan(plan._h, t.data_ptr(), xy.data_ptr(), 4, 4, 1.0, rings.data_ptr(),
+                                    ws.data_ptr(), 1024, None) == _lib.STEM_ERR_NOMEM
+    assert lib.stem_multislice_scan(plan._h, t.data_ptr(), xy.data_ptr(), 4, 0, 1.0, rings.data_ptr(),
+                                    ws.data_ptr(), ws.numel(), None) == _lib.STEM_ERR_INVALID
+    torch.cuda.synchronize()
+
+
+# --------------------------------------------------------------------- PRISM
+def _small_prism_case(n=128, f=4, slices=4, atoms=60, seed=21):
+    w = W.Workload("p", (24.0, 24.0, 8.0), atoms, n, slices, 2.0, 200.0, 20.0, 8, 2.0, 60, f=(f,))
+    xyz, gauss = W.atoms(w, seed=seed)
+    return w, xyz, gauss
+
+
+def test_prism_beams_match_oracle(api):
+    w, _, _ = _small_prism_case()
+    plan = api.Plan.from_workload(w)
+    p = O.params_from(w)
+    for f in (1, 2, 4, 8):
+        assert np.array_equal(plan.prism_beams(f), O.prism_beams(p, f).astype(np.int32))
+
+
+@pytest.mark.parametrize("f", [1, 4])
+def test_prism_smatrix_beams_vs_oracle(api, f):
+    w, xyz, gauss = _small_prism_case(f=f)
+    plan = api.Plan.from_workload(w)
+    p, tref = _oracle_trans(w, xyz, gauss)
+    beams = O.prism_beams(p, f)
+    sm = plan.prism_smatrix(dev(tref, torch.complex64), f, "f32", batch=7)
+    got = sm.beams_real_space().cpu().numpy()
+    pick = np.unique(np.linspace(0, len(beams) - 1, 9).astype(int))
+    ref = O.prism_smatrix(p, tref, beams[pick])
+    for k, b in enumerate(pick):
+        e = np.linalg.norm(got[b] - ref[k]) / np.linalg.norm(ref[k])
+        assert e <= 2e-5, (b, e)
+
+
+def test_prism_f1_equals_multislice_on_gpu(api):
+    w, xyz, gauss = _small_prism_case(n=64, f=1, slices=3)
+    plan = api.Plan.from_workload(w)
+    p, tref = _oracle_trans(w, xyz, gauss)
+    t = dev(tref, torch.complex64)
+    xy = W.random_positions(w, 11, seed=5)
+    sm = plan.prism_smatrix(t, 1, "f32", batch=64)
+    pr = plan.prism_output(sm, dev(xy), chunk=5).cpu().numpy()
+    ms = plan.multislice(t, dev(xy), batch=11).cpu().numpy()
+    ref = O.multislice_rings(p, tref, xy)
+    check_rings(pr, ref, FP32_TOL)
+    check_rings(ms, ref, FP32_TOL)
+
+
+@pytest.mark.parametrize("f", [2, 4, 8])
+def test_prism_output_vs_oracle(api, f):
+    w, xyz, gauss = _small_prism_case(f=f)
+    plan = api.Plan.from_workload(w)
+    p, tref = _oracle_trans(w, xyz, gauss)
+    beams = O.prism_beams(p, f)
+    sm = plan.prism_smatrix(dev(tref, torch.complex64), f, "f32", batch=32)
+    xy = np.concatenate([W.scan_positions(w, scan=6), W.random_positions(w, 7, seed=9)])
+    got = plan.prism_output(sm, dev(xy), chunk=16).cpu().numpy()
+    sref = O.prism_smatrix(p, tref, beams)
+    ref = O.prism_rings(p, sref, beams, f, xy)
+    check_rings(got, ref, FP32_TOL)
+    # stage-wise: the window beam sum on the GPU's own S-matrix
+    s_gpu = sm.beams_real_space().cpu().numpy().astype(np.complex128)
+    win = plan.prism_windows(sm, dev(xy[:5])).cpu().numpy()
+    wref = O.prism_window_waves(p, s_gpu, beams, f, xy[:5])
+    assert np.linalg.norm(win - wref) / np.linalg.norm(wref) <= 1e-5
+
+
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+def test_prism_reduced_precision_storage(api, storage):
+    w, xyz, gauss = _small_prism_case(f=4)
+    plan = api.Plan.from_workload(w)
+    p, tref = _oracle_trans(w, xyz, gauss)
+    beams = O.prism_beams(p, 4)
+    t = dev(tref, torch.complex64)
+    sm = plan.prism_smatrix(t, 4, storage, batch=16)
+    sc = sm.scales().cpu().numpy()
+    assert np.all(sc[: sm.n_beams] > 0) and np.all(np.log2(sc) == np.round(np.log2(sc)))
+    assert np.all(np.abs(sm.data().float().cpu().numpy()) <= 1.0)
+    xy = W.scan_positions(w, scan=5)
+    got = plan.prism_output(sm, dev(xy), chunk=25, engine="simt").cpu().numpy()
+    ref = O.prism_rings(p, O.prism_smatrix(p, tref, beams), beams, 4, xy)
+    check_rings(got, ref, LOWP_TOL)
+
+
+def test_prism_free_space_closed_form(api):
+    w, _, _ = _small_prism_case(n=128, f=4)
+    plan = api.Plan.from_workload(w)
+    p = O.params_from(w)
+    t = torch.ones((w.n_slices, 128, 128), dtype=torch.complex64, device="cuda")
+    sm = plan.prism_smatrix(t, 4, "f32")
+    xy = W.random_positions(w, 6, seed=1)
+    got = plan.prism_output(sm, dev(xy)).cpu().numpy()
+    beams = O.prism_beams(p, 4)
+    tab = O.ring_table(p)
+    counts = np.zeros(p.n_rings)
+    for m, n in beams:
+        r = tab[n % 128, m % 128]
+        if r >= 0:
+            counts[r] += 1
+    assert np.max(np.abs(got - counts[None] / len(beams))) <= 1e-5

@@ -211,6 +211,10 @@ stem_status stem_fft2(int32_t n, int64_t batch, int32_t inverse, void* data, voi
 size_t stem_footprint_bytes(const stem_params* params, int32_t algo, int32_t f,
                             stem_storage storage, int64_t n_probes, int32_t batch);
 
+/* Number of CUDA kernels this library has launched in this process (all
+ * devices, all streams); for launch accounting in benchmarks. */
+uint64_t stem_launch_count(void);
+
 const char* stem_status_string(stem_status status);
 
 #ifdef __cplusplus

@@ -38,6 +38,7 @@ class StemError(RuntimeError):
 # name -> (restype, argtypes)
 SIGNATURES = {
     "stem_status_string": (c_char_p, [c_int32]),
+    "stem_launch_count": (ctypes.c_uint64, []),
     "stem_plan_create": (c_int32, [POINTER(StemParams), POINTER(c_void_p)]),
     "stem_plan_destroy": (None, [c_void_p]),
     "stem_plan_constants": (c_int32, [c_void_p, POINTER(c_double), POINTER(c_double), POINTER(c_int32)]),

@@ -108,7 +108,11 @@ class Plan:
             pass
 
     # ------------------------------------------------------------------ potentials
-    def slice_potentials(self, xyz: torch.Tensor, gauss: torch.Tensor, want_v: bool = False):
+    def potentials_workspace(self, n_atoms: int) -> torch.Tensor:
+        return _workspace(_lib.load().stem_slice_potentials_workspace(self._h, n_atoms), self.device)
+
+    def slice_potentials(self, xyz: torch.Tensor, gauss: torch.Tensor, want_v: bool = False,
+                         out: Optional[torch.Tensor] = None, workspace: Optional[torch.Tensor] = None):
         """t_n = exp(i sigma V_n) as complex64 [S, N, N] (and V_n float32 if want_v)."""
         lib = _lib.load()
         xyz = _need(xyz, torch.float64, "xyz")
@@ -116,10 +120,11 @@ class Plan:
         na = xyz.shape[0]
         if xyz.shape != (na, 3) or gauss.shape != (na, 4):
             raise ValueError("xyz must be [n,3] and gauss [n,4]")
-        trans = torch.empty((self.n_slices, self.n, self.n), dtype=torch.complex64, device=self.device)
-        v = torch.empty((self.n_slices, self.n, self.n), dtype=torch.float32, device=self.device) if want_v else None
-        nws = lib.stem_slice_potentials_workspace(self._h, na)
-        ws = _workspace(nws, self.device)
+        shape = (self.n_slices, self.n, self.n)
+        trans = out if out is not None else torch.empty(shape, dtype=torch.complex64, device=self.device)
+        trans = _need(trans, torch.complex64, "out", shape)
+        v = torch.empty(shape, dtype=torch.float32, device=self.device) if want_v else None
+        ws = workspace if workspace is not None else self.potentials_workspace(na)
         check(lib.stem_slice_potentials(self._h, _ptr(xyz), _ptr(gauss), na, _ptr(v), _ptr(trans), _ptr(ws),
                                         ws.numel(), _stream(self.device)), "stem_slice_potentials")
         return (trans, v) if want_v else trans

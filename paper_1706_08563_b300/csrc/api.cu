@@ -5,6 +5,7 @@
 // PRISM beam lists) and sequences the kernels on the caller's stream.  No
 // simulation arithmetic runs on the host.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -12,6 +13,11 @@
 #include "internal.h"
 
 using namespace stem;
+
+namespace stem {
+static std::atomic<unsigned long long> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+}  // namespace stem
 
 namespace {
 
@@ -72,6 +78,8 @@ int count_beams(const stem_params* p, int f, double lam) {
 }  // namespace
 
 extern "C" {
+
+uint64_t stem_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
 const char* stem_status_string(stem_status s) {
   switch (s) {
@@ -201,8 +209,8 @@ stem_status stem_plan_constants(stem_plan pl, double* lambda_a, double* sigma, i
 
 // ----------------------------------------------------------------------------- potentials
 size_t stem_slice_potentials_workspace(stem_plan pl, int64_t n_atoms) {
-  (void)pl;
-  return potential_workspace(n_atoms);
+  if (!pl || n_atoms < 0 || pl->n < 64) return 0;
+  return potential_workspace(n_atoms, pl->n, pl->p.n_slices);
 }
 
 stem_status stem_slice_potentials(stem_plan pl, const double* xyz, const float* gauss, int64_t n_atoms, float* v_out,
@@ -210,7 +218,7 @@ stem_status stem_slice_potentials(stem_plan pl, const double* xyz, const float* 
   if (!pl || n_atoms < 0 || (n_atoms > 0 && (!xyz || !gauss)) || (!v_out && !trans_out) || !ws)
     return STEM_ERR_INVALID;
   if (pl->n < 64) return STEM_ERR_UNSUPPORTED;
-  if (ws_bytes < potential_workspace(n_atoms)) return STEM_ERR_NOMEM;
+  if (ws_bytes < potential_workspace(n_atoms, pl->n, pl->p.n_slices)) return STEM_ERR_NOMEM;
   return cuda_status(launch_potentials(pl->p, pl->sigma, xyz, gauss, n_atoms, v_out,
                                        static_cast<float2*>(trans_out), ws, as_stream(stream)));
 }

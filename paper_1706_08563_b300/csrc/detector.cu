@@ -36,7 +36,7 @@ cudaError_t launch_readout(int w, const float2* psi_k, int64_t batch, const uint
   if (batch <= 0) return cudaSuccess;
   const int64_t npix = (int64_t)w * w;
   dim3 grid((unsigned)((npix + kReadPix - 1) / kReadPix), (unsigned)batch);
-  k_readout<<<grid, kReadThreads, n_rings * sizeof(float), s>>>(psi_k, npix, lut, n_rings, scale, rings);
+  note_launch(), k_readout<<<grid, kReadThreads, n_rings * sizeof(float), s>>>(psi_k, npix, lut, n_rings, scale, rings);
   return cudaGetLastError();
 }
 

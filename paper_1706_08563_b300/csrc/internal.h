@@ -38,11 +38,14 @@ struct PassArgs {
 enum RowMode { ROW_SLICE = 0, ROW_BEAM0 = 1, ROW_IFFT_MAX = 2, ROW_FFT = 3, ROW_IFFT = 4 };
 enum ColMode { COL_SLICE = 0, COL_DET = 1, COL_PROBE_INIT = 2, COL_FFT = 3, COL_IFFT = 4 };
 
+// Counts this library's kernel launches (stem_launch_count); called at every launch site.
+void note_launch();
+
 cudaError_t launch_row_pass(int n, int mode, const PassArgs& a, cudaStream_t s);
 cudaError_t launch_col_pass(int n, int mode, const PassArgs& a, cudaStream_t s);
 
 // Potentials (potential.cu)
-size_t potential_workspace(int64_t n_atoms);
+size_t potential_workspace(int64_t n_atoms, int n, int n_slices);
 cudaError_t launch_potentials(const stem_params& p, double sigma, const double* xyz, const float* gauss,
                               int64_t n_atoms, float* v_out, float2* t_out, void* ws, cudaStream_t s);
 

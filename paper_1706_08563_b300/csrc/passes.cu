@@ -203,7 +203,7 @@ static cudaError_t row_launch(const PassArgs& a, cudaStream_t s) {
   cudaError_t e = set_smem(k_row_pass<N, MODE>, Cfg::SMEM, flag);
   if (e != cudaSuccess) return e;
   dim3 grid(a.batch, N / Cfg::ROWS);
-  k_row_pass<N, MODE><<<grid, Cfg::THREADS, Cfg::SMEM, s>>>(a);
+  note_launch(), k_row_pass<N, MODE><<<grid, Cfg::THREADS, Cfg::SMEM, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -215,7 +215,7 @@ static cudaError_t col_launch(const PassArgs& a, cudaStream_t s) {
   cudaError_t e = set_smem(k_col_pass<N, MODE>, Cfg::FFT_SMEM + kMaxRings * sizeof(float), flag);
   if (e != cudaSuccess) return e;
   dim3 grid(N / Cfg::C, a.batch);
-  k_col_pass<N, MODE><<<grid, Cfg::THREADS, smem, s>>>(a);
+  note_launch(), k_col_pass<N, MODE><<<grid, Cfg::THREADS, smem, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -7,30 +7,53 @@
 // periodic images on the square support |dx|, |dy| <= Rc = 8 max(s1, s2).
 // Eq. 1's transmission function t_n = exp(i sigma V_n) is written alongside.
 //
-// Deterministic gather: a CTA owns a 32 x 32 pixel tile and a chunk of 8
-// slices; it streams the atom list, compacts (in atom order) the atoms of its
-// slices whose support touches the tile, and every thread adds them, in that
-// order, to the pixels it owns.
+// Layout of the work: atoms are counting-sorted by (slice, 32 x 32 pixel cell
+// of their centre).  A CTA owns one pixel tile and walks the slices; for each
+// slice it visits the cells within reach of the largest cutoff and adds every
+// atom there to the pixels it owns.  Sums are accumulated in 2^-32 fixed point
+// (64-bit integers), so the result does not depend on the order in which the
+// counting sort placed the atoms.
 #include "internal.h"
 
 namespace stem {
 
 struct AtomRec {
-  int slice;
   int jx, iy;      // pixel of the atom position, floor(x / dx) mod N
   float fx, fy;    // fractional pixel offset in [0, 1)
   float a1, a2;
-  float inv2s1x, inv2s2x;   // dx^2 / (2 s^2): Gaussian exponent per squared pixel along x
-  float inv2s1y, inv2s2y;   // ... along y
+  float e1x, e2x;  // dx^2 / (2 s^2): Gaussian exponent per squared pixel along x
+  float e1y, e2y;  // ... along y
   float rcx, rcy;  // cutoff in pixels
 };
 
 constexpr int kTile = 32;
-constexpr int kSliceChunk = 8;
 constexpr int kPotThreads = 256;
+constexpr float kFix = 4294967296.0f;   // 2^32
+
+struct PotWs {
+  size_t recs, key, sorted, counts, offsets, reach, total;
+};
+
+static size_t al(size_t x) { return (x + 255) / 256 * 256; }
+
+static PotWs pot_layout(int64_t n_atoms, int n, int n_slices) {
+  const size_t na = (size_t)(n_atoms > 0 ? n_atoms : 1);
+  const size_t keys = (size_t)n_slices * (n / kTile) * (n / kTile);
+  PotWs L;
+  size_t off = 0;
+  L.recs = off;    off += al(na * sizeof(AtomRec));
+  L.key = off;     off += al(na * sizeof(int));
+  L.sorted = off;  off += al(na * sizeof(int));
+  L.counts = off;  off += al(keys * sizeof(int));
+  L.offsets = off; off += al((keys + 1) * sizeof(int));
+  L.reach = off;   off += al(2 * sizeof(int));
+  L.total = off;
+  return L;
+}
 
 __global__ void k_atom_prep(const double* __restrict__ xyz, const float* __restrict__ gauss, int64_t n_atoms,
-                            int n, int n_slices, double dz, double dx, double dy, AtomRec* __restrict__ out) {
+                            int n, int n_slices, double dz, double dx, double dy, AtomRec* __restrict__ out,
+                            int* __restrict__ key, int* __restrict__ counts, int* __restrict__ reach) {
   const int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (a >= n_atoms) return;
   const double x = xyz[3 * a], y = xyz[3 * a + 1], z = xyz[3 * a + 2];
@@ -39,7 +62,6 @@ __global__ void k_atom_prep(const double* __restrict__ xyz, const float* __restr
   const double u = x / dx, v = y / dy;
   const double ju = floor(u), iv = floor(v);
   AtomRec r;
-  r.slice = (int)s;
   r.jx = (int)(((long long)ju % n + n) % n);
   r.iy = (int)(((long long)iv % n + n) % n);
   r.fx = (float)(u - ju);
@@ -48,26 +70,58 @@ __global__ void k_atom_prep(const double* __restrict__ xyz, const float* __restr
   const float fdx = (float)dx, fdy = (float)dy;
   r.a1 = a1;
   r.a2 = a2;
-  r.inv2s1x = fdx * fdx / (2.0f * s1 * s1);
-  r.inv2s2x = fdx * fdx / (2.0f * s2 * s2);
-  r.inv2s1y = fdy * fdy / (2.0f * s1 * s1);
-  r.inv2s2y = fdy * fdy / (2.0f * s2 * s2);
+  r.e1x = fdx * fdx / (2.0f * s1 * s1);
+  r.e2x = fdx * fdx / (2.0f * s2 * s2);
+  r.e1y = fdy * fdy / (2.0f * s1 * s1);
+  r.e2y = fdy * fdy / (2.0f * s2 * s2);
   const float rc = 8.0f * fmaxf(s1, s2);
   r.rcx = rc / fdx;
   r.rcy = rc / fdy;
   out[a] = r;
+  const int cells = n / kTile;
+  const int k = ((int)s * cells + r.iy / kTile) * cells + r.jx / kTile;
+  key[a] = k;
+  atomicAdd(counts + k, 1);
+  // reach in cells: a pixel of a tile can be touched by atoms whose centre cell
+  // is up to ceil((rc + 1) / 32) cells away
+  atomicMax(reach, (int)ceilf((r.rcx + 1.0f) / (float)kTile));
+  atomicMax(reach + 1, (int)ceilf((r.rcy + 1.0f) / (float)kTile));
 }
 
-// Does [c - r, c + r] (pixel units, any periodic image) touch [lo, lo + len - 1]?
-// Widened by one pixel on each side; the exact support test is per pixel.
-__device__ __forceinline__ bool touches(float c, float r, int lo, int len, int n) {
-  const float a = (float)lo - c - r - 1.0f;
-  const float b = (float)(lo + len - 1) - c + r + 1.0f;
-  return floorf(b / (float)n) * (float)n >= a;
+// Exclusive scan of counts into offsets; counts become zeroed fill cursors.
+__global__ void k_pot_scan(int* __restrict__ counts, int n_keys, int* __restrict__ offsets) {
+  __shared__ int s_a[1024];
+  const int per = (n_keys + blockDim.x - 1) / blockDim.x;
+  const int lo = min((int)threadIdx.x * per, n_keys), hi = min(lo + per, n_keys);
+  int a = 0;
+  for (int i = lo; i < hi; ++i) a += counts[i];
+  s_a[threadIdx.x] = a;
+  __syncthreads();
+  for (int d = 1; d < (int)blockDim.x; d <<= 1) {
+    const int va = threadIdx.x >= d ? s_a[threadIdx.x - d] : 0;
+    __syncthreads();
+    s_a[threadIdx.x] += va;
+    __syncthreads();
+  }
+  a = s_a[threadIdx.x] - a;
+  for (int i = lo; i < hi; ++i) {
+    offsets[i] = a;
+    a += counts[i];
+    counts[i] = 0;
+  }
+  if (threadIdx.x == blockDim.x - 1) offsets[n_keys] = s_a[threadIdx.x];
+}
+
+__global__ void k_pot_fill(const int* __restrict__ key, int64_t n_atoms, const int* __restrict__ offsets,
+                           int* __restrict__ cursor, int* __restrict__ sorted) {
+  const int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (a >= n_atoms) return;
+  const int k = key[a];
+  sorted[offsets[k] + atomicAdd(cursor + k, 1)] = (int)a;
 }
 
 // Sum over periodic images of the two Gaussians along one axis (pixel units).
-__device__ __forceinline__ void axis_terms(float d0, float rc, float i1, float i2, int n, float& g1, float& g2) {
+__device__ __forceinline__ void axis_terms(float d0, float rc, float e1, float e2, int n, float& g1, float& g2) {
   d0 -= (float)n * rintf(d0 / (float)n);
   g1 = 0.0f;
   g2 = 0.0f;
@@ -76,100 +130,98 @@ __device__ __forceinline__ void axis_terms(float d0, float rc, float i1, float i
     const float d = d0 + (float)(k * n);
     if (fabsf(d) <= rc) {
       const float d2 = d * d;
-      g1 += expf(-d2 * i1);
-      g2 += expf(-d2 * i2);
+      g1 += expf(-d2 * e1);
+      g2 += expf(-d2 * e2);
     }
   }
 }
 
-__global__ void __launch_bounds__(kPotThreads) k_potential(const AtomRec* __restrict__ atoms, int64_t n_atoms, int n,
-                                                           int n_slices, float sigma, float* __restrict__ v_out,
+__global__ void __launch_bounds__(kPotThreads) k_potential(const AtomRec* __restrict__ recs,
+                                                           const int* __restrict__ sorted,
+                                                           const int* __restrict__ offsets,
+                                                           const int* __restrict__ reach, int n, int n_slices,
+                                                           float sigma, float* __restrict__ v_out,
                                                            float2* __restrict__ t_out) {
-  __shared__ float acc[kSliceChunk][kTile * kTile];
-  __shared__ AtomRec list[kPotThreads];
-  __shared__ int warp_count[kPotThreads / 32];
-  __shared__ int n_list;
-  const int tiles_x = n / kTile;
-  const int tx0 = (blockIdx.x % tiles_x) * kTile;
-  const int ty0 = (blockIdx.x / tiles_x) * kTile;
-  const int s0 = blockIdx.y * kSliceChunk;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-
-  for (int i = threadIdx.x; i < kSliceChunk * kTile * kTile; i += kPotThreads) (&acc[0][0])[i] = 0.0f;
-
-  // thread owns column tid % 32 and rows tid / 32 + 8 q, q < 4
-  const int j = tx0 + (threadIdx.x % kTile);
-  for (int64_t base = 0; base < n_atoms; base += kPotThreads) {
-    const int64_t a = base + threadIdx.x;
-    bool keep = false;
-    AtomRec r;
-    if (a < n_atoms) {
-      r = atoms[a];
-      keep = r.slice >= s0 && r.slice < s0 + kSliceChunk &&
-             touches((float)r.jx + r.fx, r.rcx, tx0, kTile, n) &&
-             touches((float)r.iy + r.fy, r.rcy, ty0, kTile, n);
-    }
-    const unsigned ballot = __ballot_sync(0xffffffffu, keep);
-    if (lane == 0) warp_count[warp] = __popc(ballot);
-    __syncthreads();
-    int before = 0, total = 0;
-    for (int w = 0; w < kPotThreads / 32; ++w) {
-      before += (w < warp) ? warp_count[w] : 0;
-      total += warp_count[w];
-    }
-    if (keep) list[before + __popc(ballot & ((1u << lane) - 1u))] = r;
-    if (threadIdx.x == 0) n_list = total;
-    __syncthreads();
-    const int cnt = n_list;
-    for (int k = 0; k < cnt; ++k) {
-      const AtomRec& at = list[k];
-      float* out = acc[at.slice - s0];
-      float gx1, gx2;
-      axis_terms((float)(j - at.jx) - at.fx, at.rcx, at.inv2s1x, at.inv2s2x, n, gx1, gx2);
-      if (gx1 == 0.0f && gx2 == 0.0f) continue;
+  constexpr int PX = kTile * kTile / kPotThreads;   // pixels per thread (one column, PX rows)
+  const int cells = n / kTile;
+  const int cx = blockIdx.x % cells, cy = blockIdx.x / cells;
+  const int j = cx * kTile + (threadIdx.x % kTile);
+  const int i0 = cy * kTile + threadIdx.x / kTile;
+  const int rx = __ldg(reach), ry = __ldg(reach + 1);
+  // distinct neighbour cells only (small grids wrap onto themselves)
+  const int nx = min(2 * rx + 1, cells), ny = min(2 * ry + 1, cells);
+  for (int s = 0; s < n_slices; ++s) {
+    long long acc[PX];
 #pragma unroll
-      for (int q = 0; q < kTile * kTile / kPotThreads; ++q) {
-        const int p = threadIdx.x + q * kPotThreads;
-        const int i = ty0 + (p / kTile);
-        float gy1, gy2;
-        axis_terms((float)(i - at.iy) - at.fy, at.rcy, at.inv2s1y, at.inv2s2y, n, gy1, gy2);
-        out[p] += at.a1 * gx1 * gy1 + at.a2 * gx2 * gy2;
+    for (int q = 0; q < PX; ++q) acc[q] = 0;
+    for (int oy = 0; oy < ny; ++oy) {
+      const int ccy = ((cy - ry + oy) % cells + cells) % cells;
+      for (int ox = 0; ox < nx; ++ox) {
+        const int ccx = ((cx - rx + ox) % cells + cells) % cells;
+        const int k = (s * cells + ccy) * cells + ccx;
+        const int b = __ldg(offsets + k), e = __ldg(offsets + k + 1);
+        for (int idx = b; idx < e; ++idx) {
+          const AtomRec at = recs[__ldg(sorted + idx)];
+          float gx1, gx2;
+          axis_terms((float)(j - at.jx) - at.fx, at.rcx, at.e1x, at.e2x, n, gx1, gx2);
+          if (gx1 == 0.0f && gx2 == 0.0f) continue;
+#pragma unroll
+          for (int q = 0; q < PX; ++q) {
+            const int i = i0 + q * (kPotThreads / kTile);
+            float gy1, gy2;
+            axis_terms((float)(i - at.iy) - at.fy, at.rcy, at.e1y, at.e2y, n, gy1, gy2);
+            const float v = at.a1 * gx1 * gy1 + at.a2 * gx2 * gy2;
+            acc[q] += __float2ll_rn(v * kFix);
+          }
+        }
       }
     }
-    __syncthreads();
-  }
-
-  for (int sl = 0; sl < kSliceChunk && s0 + sl < n_slices; ++sl) {
-    for (int p = threadIdx.x; p < kTile * kTile; p += kPotThreads) {
-      const int jj = tx0 + (p % kTile), i = ty0 + (p / kTile);
-      const size_t idx = ((size_t)(s0 + sl) * n + i) * n + jj;
-      const float v = acc[sl][p];
+#pragma unroll
+    for (int q = 0; q < PX; ++q) {
+      const int i = i0 + q * (kPotThreads / kTile);
+      const size_t idx = ((size_t)s * n + i) * n + j;
+      const float v = (float)((double)acc[q] * (1.0 / 4294967296.0));
       if (v_out) v_out[idx] = v;
       if (t_out) {
-        float s, c;
-        sincosf(sigma * v, &s, &c);
-        t_out[idx] = make_float2(c, s);
+        float sn, cs;
+        sincosf(sigma * v, &sn, &cs);
+        t_out[idx] = make_float2(cs, sn);
       }
     }
   }
 }
 
-size_t potential_workspace(int64_t n_atoms) { return (size_t)(n_atoms > 0 ? n_atoms : 1) * sizeof(AtomRec); }
+size_t potential_workspace(int64_t n_atoms, int n, int n_slices) { return pot_layout(n_atoms, n, n_slices).total; }
 
 cudaError_t launch_potentials(const stem_params& p, double sigma, const double* xyz, const float* gauss,
                               int64_t n_atoms, float* v_out, float2* t_out, void* ws, cudaStream_t s) {
   const int n = p.n;
-  AtomRec* atoms = static_cast<AtomRec*>(ws);
+  const PotWs L = pot_layout(n_atoms, n, p.n_slices);
+  char* base = static_cast<char*>(ws);
+  AtomRec* recs = reinterpret_cast<AtomRec*>(base + L.recs);
+  int* key = reinterpret_cast<int*>(base + L.key);
+  int* sorted = reinterpret_cast<int*>(base + L.sorted);
+  int* counts = reinterpret_cast<int*>(base + L.counts);
+  int* offsets = reinterpret_cast<int*>(base + L.offsets);
+  int* reach = reinterpret_cast<int*>(base + L.reach);
+  const int n_keys = p.n_slices * (n / kTile) * (n / kTile);
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(counts, 0, n_keys * sizeof(int), s)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(reach, 0, 2 * sizeof(int), s)) != cudaSuccess) return e;
   if (n_atoms > 0) {
-    const int threads = 256;
-    const unsigned blocks = (unsigned)((n_atoms + threads - 1) / threads);
-    k_atom_prep<<<blocks, threads, 0, s>>>(xyz, gauss, n_atoms, n, p.n_slices, p.slice_dz, p.cell[0] / n,
-                                           p.cell[1] / n, atoms);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    const unsigned blocks = (unsigned)((n_atoms + 255) / 256);
+    note_launch(), k_atom_prep<<<blocks, 256, 0, s>>>(xyz, gauss, n_atoms, n, p.n_slices, p.slice_dz, p.cell[0] / n, p.cell[1] / n,
+                                       recs, key, counts, reach);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  dim3 grid((n / kTile) * (n / kTile), (p.n_slices + kSliceChunk - 1) / kSliceChunk);
-  k_potential<<<grid, kPotThreads, 0, s>>>(atoms, n_atoms, n, p.n_slices, (float)sigma, v_out, t_out);
+  note_launch(), k_pot_scan<<<1, 1024, 0, s>>>(counts, n_keys, offsets);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (n_atoms > 0) {
+    note_launch(), k_pot_fill<<<(unsigned)((n_atoms + 255) / 256), 256, 0, s>>>(key, n_atoms, offsets, counts, sorted);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  note_launch(), k_potential<<<(n / kTile) * (n / kTile), kPotThreads, 0, s>>>(recs, sorted, offsets, reach, n, p.n_slices,
+                                                                (float)sigma, v_out, t_out);
   return cudaGetLastError();
 }
 

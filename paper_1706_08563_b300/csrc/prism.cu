@@ -116,9 +116,9 @@ static void store_typed(const float2* waves, int nb, int npix, int b0, int n_bea
                         const SmatLayout& L, float* scales, char* data, cudaStream_t s) {
   using T = typename Elem<S>::T;
   dim3 grid(npix / 32, (nb + 31) / 32);
-  k_smatrix_store<S><<<grid, 256, 0, s>>>(waves, nb, npix, b0, beam_max, L.nbp, scales, reinterpret_cast<T*>(data));
+  note_launch(), k_smatrix_store<S><<<grid, 256, 0, s>>>(waves, nb, npix, b0, beam_max, L.nbp, scales, reinterpret_cast<T*>(data));
   if (b0 + nb >= n_beams_total && L.nbp > n_beams_total)
-    k_smatrix_pad<S><<<1024, 256, 0, s>>>(npix, n_beams_total, L.nbp, scales, reinterpret_cast<T*>(data));
+    note_launch(), k_smatrix_pad<S><<<1024, 256, 0, s>>>(npix, n_beams_total, L.nbp, scales, reinterpret_cast<T*>(data));
 }
 
 cudaError_t launch_smatrix_store(const float2* waves, int nb, int n, int b0, int n_beams_total,
@@ -366,15 +366,15 @@ cudaError_t prism_windows_chunk(const OutputArgs& o, const double* probe_xy, int
   cudaError_t e;
 
   dim3 cg((o.nbp + 127) / 128, np);
-  k_coefficients<<<cg, 128, 0, s>>>(probe_xy, o.beams, o.n_beams, o.nbp, o.scales, 1.0 / o.lx, 1.0 / o.ly,
+  note_launch(), k_coefficients<<<cg, 128, 0, s>>>(probe_xy, o.beams, o.n_beams, o.nbp, o.scales, 1.0 / o.lx, 1.0 / o.ly,
                                     o.coef_norm, coef);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(counts, 0, n_tiles * sizeof(int), s)) != cudaSuccess) return e;
-  k_origins<<<(np + 127) / 128, 128, 0, s>>>(probe_xy, np, n, w, o.dx, o.dy, origin, counts);
+  note_launch(), k_origins<<<(np + 127) / 128, 128, 0, s>>>(probe_xy, np, n, w, o.dx, o.dy, origin, counts);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  k_scan_tiles<<<1, 1024, 0, s>>>(counts, n_tiles, kGroup, offsets, work);
+  note_launch(), k_scan_tiles<<<1, 1024, 0, s>>>(counts, n_tiles, kGroup, offsets, work);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  k_fill_tiles<<<(np + 127) / 128, 128, 0, s>>>(origin, np, n, w, offsets, counts, list);
+  note_launch(), k_fill_tiles<<<(np + 127) / 128, 128, 0, s>>>(origin, np, n, w, offsets, counts, list);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
 
   int dev = 0, sms = 148;
@@ -383,15 +383,15 @@ cudaError_t prism_windows_chunk(const OutputArgs& o, const double* probe_xy, int
   const unsigned grid = (unsigned)sms * 4;
   switch (o.storage) {
     case STEM_F32:
-      k_beam_sum_simt<STEM_F32><<<grid, 256, 0, s>>>(static_cast<const float*>(o.sdata), n, w, o.nbp, coef, origin,
+      note_launch(), k_beam_sum_simt<STEM_F32><<<grid, 256, 0, s>>>(static_cast<const float*>(o.sdata), n, w, o.nbp, coef, origin,
                                                      offsets, work, list, n_tiles, windows);
       break;
     case STEM_F16:
-      k_beam_sum_simt<STEM_F16><<<grid, 256, 0, s>>>(static_cast<const __half*>(o.sdata), n, w, o.nbp, coef, origin,
+      note_launch(), k_beam_sum_simt<STEM_F16><<<grid, 256, 0, s>>>(static_cast<const __half*>(o.sdata), n, w, o.nbp, coef, origin,
                                                      offsets, work, list, n_tiles, windows);
       break;
     case STEM_BF16:
-      k_beam_sum_simt<STEM_BF16><<<grid, 256, 0, s>>>(static_cast<const __nv_bfloat16*>(o.sdata), n, w, o.nbp, coef,
+      note_launch(), k_beam_sum_simt<STEM_BF16><<<grid, 256, 0, s>>>(static_cast<const __nv_bfloat16*>(o.sdata), n, w, o.nbp, coef,
                                                       origin, offsets, work, list, n_tiles, windows);
       break;
     default: return cudaErrorInvalidValue;

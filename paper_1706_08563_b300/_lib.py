@@ -10,7 +10,8 @@ import ctypes
 import os
 from ctypes import POINTER, c_char_p, c_double, c_float, c_int32, c_int64, c_size_t, c_void_p
 
-LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libstem.so")
+# STEM_LIB may name another build of the same library (for example a tuning variant).
+LIB_PATH = os.environ.get("STEM_LIB") or os.path.join(os.path.dirname(os.path.abspath(__file__)), "libstem.so")
 
 STEM_OK = 0
 STEM_ERR_INVALID = -1

@@ -7,7 +7,8 @@
 // w^(r (j mod Ns)) with w = exp(-+2 pi i / (Ns R_s)), runs a radix-R_s DFT in
 // registers and writes output k to (j / Ns) Ns R_s + (j mod Ns) + k Ns.  The
 // first stage has radix E and needs no twiddles; stages exchange data through
-// shared memory.
+// shared memory, and the later stages read their twiddles from a per-block
+// shared-memory table.
 //
 // Register convention at entry and exit: thread t holds element t + T*q in
 // v[q], q in [0, E).  So a forward transform can feed an inverse one (or a
@@ -17,6 +18,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+
 namespace stem {
 
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
@@ -24,45 +26,63 @@ __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
+// a * conj(b)
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.y, b.x, -a.x * b.y));
+}
 __device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
 __device__ __forceinline__ float cabs2(float2 a) { return fmaf(a.x, a.x, a.y * a.y); }
 
-// exp(-2 pi i j / 32) for j in [0, 16): the twiddles of radix-2 decimation in
-// frequency for every transform length up to 32.
-__device__ __forceinline__ float2 w32(int j) {
+// exp(-2 pi i j / 64) for j in [0, 32): the twiddles of radix-2 decimation in
+// frequency for every transform length up to 64.
+__device__ __forceinline__ float2 w64(int j) {
   switch (j) {
-    case 1: return make_float2(9.807852804e-01f, -1.950903220e-01f);
-    case 2: return make_float2(9.238795325e-01f, -3.826834324e-01f);
-    case 3: return make_float2(8.314696123e-01f, -5.555702330e-01f);
-    case 4: return make_float2(7.071067812e-01f, -7.071067812e-01f);
-    case 5: return make_float2(5.555702330e-01f, -8.314696123e-01f);
-    case 6: return make_float2(3.826834324e-01f, -9.238795325e-01f);
-    case 7: return make_float2(1.950903220e-01f, -9.807852804e-01f);
-    case 9: return make_float2(-1.950903220e-01f, -9.807852804e-01f);
-    case 10: return make_float2(-3.826834324e-01f, -9.238795325e-01f);
-    case 11: return make_float2(-5.555702330e-01f, -8.314696123e-01f);
-    case 12: return make_float2(-7.071067812e-01f, -7.071067812e-01f);
-    case 13: return make_float2(-8.314696123e-01f, -5.555702330e-01f);
-    case 14: return make_float2(-9.238795325e-01f, -3.826834324e-01f);
-    case 15: return make_float2(-9.807852804e-01f, -1.950903220e-01f);
+    case 1: return make_float2(9.951847267e-01f, -9.801714033e-02f);
+    case 2: return make_float2(9.807852804e-01f, -1.950903220e-01f);
+    case 3: return make_float2(9.569403357e-01f, -2.902846773e-01f);
+    case 4: return make_float2(9.238795325e-01f, -3.826834324e-01f);
+    case 5: return make_float2(8.819212643e-01f, -4.713967368e-01f);
+    case 6: return make_float2(8.314696123e-01f, -5.555702330e-01f);
+    case 7: return make_float2(7.730104534e-01f, -6.343932842e-01f);
+    case 9: return make_float2(6.343932842e-01f, -7.730104534e-01f);
+    case 10: return make_float2(5.555702330e-01f, -8.314696123e-01f);
+    case 11: return make_float2(4.713967368e-01f, -8.819212643e-01f);
+    case 12: return make_float2(3.826834324e-01f, -9.238795325e-01f);
+    case 13: return make_float2(2.902846773e-01f, -9.569403357e-01f);
+    case 14: return make_float2(1.950903220e-01f, -9.807852804e-01f);
+    case 15: return make_float2(9.801714033e-02f, -9.951847267e-01f);
+    case 17: return make_float2(-9.801714033e-02f, -9.951847267e-01f);
+    case 18: return make_float2(-1.950903220e-01f, -9.807852804e-01f);
+    case 19: return make_float2(-2.902846773e-01f, -9.569403357e-01f);
+    case 20: return make_float2(-3.826834324e-01f, -9.238795325e-01f);
+    case 21: return make_float2(-4.713967368e-01f, -8.819212643e-01f);
+    case 22: return make_float2(-5.555702330e-01f, -8.314696123e-01f);
+    case 23: return make_float2(-6.343932842e-01f, -7.730104534e-01f);
+    case 25: return make_float2(-7.730104534e-01f, -6.343932842e-01f);
+    case 26: return make_float2(-8.314696123e-01f, -5.555702330e-01f);
+    case 27: return make_float2(-8.819212643e-01f, -4.713967368e-01f);
+    case 28: return make_float2(-9.238795325e-01f, -3.826834324e-01f);
+    case 29: return make_float2(-9.569403357e-01f, -2.902846773e-01f);
+    case 30: return make_float2(-9.807852804e-01f, -1.950903220e-01f);
+    case 31: return make_float2(-9.951847267e-01f, -9.801714033e-02f);
     default: return make_float2(1.0f, 0.0f);
   }
 }
 
-// d * w^j (forward) or d * conj(w)^j (inverse), w = exp(-2 pi i / 32), j < 16.
+// d * w^j (forward) or d * conj(w)^j (inverse), w = exp(-2 pi i / 64), j < 32.
 template <bool INV>
-__device__ __forceinline__ float2 tw32(float2 d, int j) {
+__device__ __forceinline__ float2 tw64(float2 d, int j) {
   if (j == 0) return d;
-  if (j == 8) return INV ? make_float2(-d.y, d.x) : make_float2(d.y, -d.x);
-  if (j == 4 || j == 12) {
+  if (j == 16) return INV ? make_float2(-d.y, d.x) : make_float2(d.y, -d.x);
+  if (j == 8 || j == 24) {
     // forward: w = h (sx - i);  d w = h (sx d.x + d.y, sx d.y - d.x)
     // inverse: w = h (sx + i);  d w = h (sx d.x - d.y, sx d.y + d.x)
     const float h = 7.071067812e-01f;
-    const float sx = (j == 4) ? 1.0f : -1.0f;
+    const float sx = (j == 8) ? 1.0f : -1.0f;
     return INV ? make_float2(h * (sx * d.x - d.y), h * (sx * d.y + d.x))
                : make_float2(h * (sx * d.x + d.y), h * (sx * d.y - d.x));
   }
-  float2 w = w32(j);
+  float2 w = w64(j);
   if (INV) w.y = -w.y;
   return cmul(d, w);
 }
@@ -74,7 +94,7 @@ __host__ __device__ constexpr int bitrev(int i, int bits) {
 }
 __host__ __device__ constexpr int ilog2(int n) { return n <= 1 ? 0 : 1 + ilog2(n >> 1); }
 
-// In-register radix-R DFT (R = 1..32, power of two), natural order in and out:
+// In-register radix-R DFT (R = 1..64, power of two), natural order in and out:
 // X[k] = sum_r x[r] exp(-+2 pi i r k / R).  Radix-2 decimation in frequency,
 // then the bit-reversal permutation as a register rename.
 template <int R, bool INV>
@@ -89,7 +109,7 @@ __device__ __forceinline__ void dft(float2* v) {
           const float2 a = v[start + k];
           const float2 b = v[start + k + span];
           v[start + k] = cadd(a, b);
-          v[start + k + span] = tw32<INV>(csub(a, b), k * (32 / (2 * span)));
+          v[start + k + span] = tw64<INV>(csub(a, b), k * (64 / (2 * span)));
         }
       }
     }
@@ -101,29 +121,26 @@ __device__ __forceinline__ void dft(float2* v) {
   }
 }
 
-// exp(-+2 pi i p / L) for 0 <= p < L (L a power of two), via the hardware
-// sine/cosine on an argument reduced into [-pi, pi].
-template <bool INV>
-__device__ __forceinline__ float2 twiddle(int p, int L) {
-  const int pp = (2 * p > L) ? p - L : p;
-  const float ang = (INV ? 6.283185307179586f : -6.283185307179586f) * (float)pp / (float)L;
-  float s, c;
-  __sincosf(ang, &s, &c);
-  return make_float2(c, s);
-}
-
 // Stage radices for each transform length: first radix E (elements per thread),
 // then up to two more.
+template <int E_, int R1_, int R2_> struct ShapeOf {
+  static constexpr int E = E_, R1 = R1_, R2 = R2_;
+};
+#ifndef STEM_FFT2048_E
+#define STEM_FFT2048_E 16
+#define STEM_FFT2048_R1 16
+#define STEM_FFT2048_R2 8
+#endif
 template <int N> struct FftShape;
-template <> struct FftShape<8>    { static constexpr int E = 8,  R1 = 1,  R2 = 1; };
-template <> struct FftShape<16>   { static constexpr int E = 4,  R1 = 4,  R2 = 1; };
-template <> struct FftShape<32>   { static constexpr int E = 8,  R1 = 4,  R2 = 1; };
-template <> struct FftShape<64>   { static constexpr int E = 8,  R1 = 8,  R2 = 1; };
-template <> struct FftShape<128>  { static constexpr int E = 16, R1 = 8,  R2 = 1; };
-template <> struct FftShape<256>  { static constexpr int E = 16, R1 = 16, R2 = 1; };
-template <> struct FftShape<512>  { static constexpr int E = 32, R1 = 16, R2 = 1; };
-template <> struct FftShape<1024> { static constexpr int E = 32, R1 = 32, R2 = 1; };
-template <> struct FftShape<2048> { static constexpr int E = 32, R1 = 8,  R2 = 8; };
+template <> struct FftShape<8>    : ShapeOf<8, 1, 1> {};
+template <> struct FftShape<16>   : ShapeOf<4, 4, 1> {};
+template <> struct FftShape<32>   : ShapeOf<8, 4, 1> {};
+template <> struct FftShape<64>   : ShapeOf<8, 8, 1> {};
+template <> struct FftShape<128>  : ShapeOf<16, 8, 1> {};
+template <> struct FftShape<256>  : ShapeOf<16, 16, 1> {};
+template <> struct FftShape<512>  : ShapeOf<32, 16, 1> {};
+template <> struct FftShape<1024> : ShapeOf<32, 32, 1> {};
+template <> struct FftShape<2048> : ShapeOf<STEM_FFT2048_E, STEM_FFT2048_R1, STEM_FFT2048_R2> {};
 
 // Shared-memory view of one transform: element idx lives at
 // base[(idx + idx / E) * STRIDE] (one pad slot per E elements keeps the
@@ -134,17 +151,54 @@ struct SmemView {
   __device__ __forceinline__ float2& at(int idx) const { return base[(idx + idx / E) * STRIDE]; }
 };
 
+// Twiddle tables of the stages after the first, kept in shared memory: stage
+// (NS, R) needs w^(r q), w = exp(-2 pi i / (NS R)), for r in [1, R) and q in
+// [0, NS), stored at [(r - 1) NS + q] so that lanes with consecutive q read
+// consecutive words.  The inverse transform multiplies by the conjugate.
+template <int N> struct TwLayout {
+  using S = FftShape<N>;
+  static constexpr int NS1 = S::E, R1 = S::R1;
+  static constexpr int NS2 = S::E * S::R1, R2 = S::R2;
+  static constexpr int SIZE1 = R1 > 1 ? (R1 - 1) * NS1 : 0;
+  static constexpr int SIZE2 = R2 > 1 ? (R2 - 1) * NS2 : 0;
+  static constexpr int OFF2 = SIZE1;
+  static constexpr int TOTAL = SIZE1 + SIZE2;
+};
+
+// Fill the table with exp(-2 pi i p / L): the argument 2 p / L is exact in FP32
+// (L is a power of two) and sincospif is accurate to about one ulp.
+template <int N>
+__device__ __forceinline__ void build_twiddles(float2* tw, int tid, int nthreads) {
+  using L = TwLayout<N>;
+  for (int i = tid; i < L::TOTAL; i += nthreads) {
+    int r, q, len;
+    if (i < L::SIZE1) {
+      r = i / L::NS1 + 1; q = i % L::NS1; len = L::NS1 * L::R1;
+    } else {
+      const int k = i - L::SIZE1;
+      r = k / L::NS2 + 1; q = k % L::NS2; len = L::NS2 * L::R2;
+    }
+    const int p = (r * q) % len;
+    float sn, cs;
+    sincospif(-2.0f * (float)p / (float)len, &sn, &cs);
+    tw[i] = make_float2(cs, sn);
+  }
+}
+
 // Stage s >= 1 on values already gathered: v[i*R + r] = in[j_i + r N/R] with
-// j_i = t + i T.  Applies twiddles and the radix-R DFTs.
+// j_i = t + i T.  Applies the table's twiddles and the radix-R DFTs.
 template <int N, int E, int R, int NS, bool INV>
-__device__ __forceinline__ void stage_compute(float2 (&v)[E], int t) {
+__device__ __forceinline__ void stage_compute(float2 (&v)[E], int t, const float2* tw) {
   constexpr int T = N / E;
 #pragma unroll
   for (int i = 0; i < E / R; ++i) {
     const int j = t + i * T;
     const int q = j & (NS - 1);
 #pragma unroll
-    for (int r = 1; r < R; ++r) v[i * R + r] = cmul(v[i * R + r], twiddle<INV>(r * q, NS * R));
+    for (int r = 1; r < R; ++r) {
+      const float2 w = tw[(r - 1) * NS + q];
+      v[i * R + r] = INV ? cmulc(v[i * R + r], w) : cmul(v[i * R + r], w);
+    }
     dft<R, INV>(&v[i * R]);
   }
 }
@@ -187,10 +241,13 @@ __device__ __forceinline__ void stage_rename(float2 (&v)[E]) {
 }
 
 // Full length-N transform over the T threads that share `sm`.  `sync` is
-// called around every shared-memory exchange (a warp or block barrier).
+// called around every shared-memory exchange (a warp or block barrier); `tw`
+// is the block's twiddle table (build_twiddles<N>).
 template <int N, bool INV, class View, class Sync>
-__device__ __forceinline__ void fft_dist(float2 (&v)[FftShape<N>::E], const View& sm, int t, Sync sync) {
+__device__ __forceinline__ void fft_dist(float2 (&v)[FftShape<N>::E], const View& sm, int t, Sync sync,
+                                         const float2* tw) {
   using S = FftShape<N>;
+  using L = TwLayout<N>;
   constexpr int E = S::E;
   dft<E, INV>(v);                                   // stage 0, butterfly j = t
   if constexpr (S::R1 > 1) {
@@ -199,13 +256,13 @@ __device__ __forceinline__ void fft_dist(float2 (&v)[FftShape<N>::E], const View
     for (int k = 0; k < E; ++k) sm.at(t * E + k) = v[k];
     sync();
     stage_load<N, E, S::R1>(v, sm, t);
-    stage_compute<N, E, S::R1, E, INV>(v, t);
+    stage_compute<N, E, S::R1, E, INV>(v, t, tw);
     if constexpr (S::R2 > 1) {
       sync();
       stage_store<N, E, S::R1, E>(v, sm, t);
       sync();
       stage_load<N, E, S::R2>(v, sm, t);
-      stage_compute<N, E, S::R2, E * S::R1, INV>(v, t);
+      stage_compute<N, E, S::R2, E * S::R1, INV>(v, t, tw + L::OFF2);
       stage_rename<E, S::R2>(v);
     } else {
       stage_rename<E, S::R1>(v);

@@ -8,6 +8,7 @@
 // (Fourier-space aperture and phase ramp, then a column IFFT); the last column
 // pass of multislice squares |FFT| and bins it into rings instead of storing
 // (|P| = 1, so the last propagator phase does not change intensities).
+#include <algorithm>
 #include <mutex>
 
 #include "fft_core.cuh"
@@ -15,171 +16,238 @@
 
 namespace stem {
 
+// Threads per row-pass CTA, columns per column-pass CTA and the minimum number
+// of resident CTAs asked of the compiler, per transform length.
+#ifndef STEM_ROW_THREADS_BIG
+#define STEM_ROW_THREADS_BIG 128
+#endif
+#ifndef STEM_COL_C_2048
+#define STEM_COL_C_2048 4
+#endif
+#ifndef STEM_MINB_1024
+#define STEM_MINB_1024 2
+#endif
+#ifndef STEM_MINB_2048
+#define STEM_MINB_2048 1
+#endif
+#ifndef STEM_PREFETCH
+#define STEM_PREFETCH 1
+#endif
+
+template <int N> constexpr int min_blocks() { return N == 2048 ? STEM_MINB_2048 : (N == 1024 ? STEM_MINB_1024 : 1); }
+
+// Ask L2 to fetch bytes that this CTA will read on its next tile, so that the
+// next tile's loads are served from L2 while this tile is being transformed.
+__device__ __forceinline__ void prefetch_l2_bulk(const void* p, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 template <int N> struct RowCfg {
   static constexpr int E = FftShape<N>::E;
   static constexpr int T = N / E;
-  static constexpr int ROWS = (256 / T) < N ? (256 / T) : N;
+  static constexpr int THR = N >= 1024 ? STEM_ROW_THREADS_BIG : 256;
+  static constexpr int ROWS = (THR / T) < N ? (THR / T) : N;
   static constexpr int THREADS = ROWS * T;
   static constexpr int ROWBUF = N + N / E;
-  static constexpr size_t SMEM = (size_t)ROWS * ROWBUF * sizeof(float2);
+  static constexpr size_t SMEM = ((size_t)ROWS * ROWBUF + TwLayout<N>::TOTAL) * sizeof(float2);
+  static constexpr int MINB = min_blocks<N>();
 };
 
 template <int N> struct ColCfg {
   static constexpr int E = FftShape<N>::E;
   static constexpr int T = N / E;
-  static constexpr int C0 = (256 / T) > 16 ? 16 : (256 / T);
+  static constexpr int C0 = N == 2048 ? STEM_COL_C_2048 : ((256 / T) > 16 ? 16 : (256 / T));
   static constexpr int C = C0 < 1 ? 1 : (C0 > N ? N : C0);
   static constexpr int THREADS = C * T;
-  static constexpr size_t FFT_SMEM = (size_t)(N + N / E) * C * sizeof(float2);
+  static constexpr size_t FFT_SMEM = ((size_t)(N + N / E) * C + TwLayout<N>::TOTAL) * sizeof(float2);
+  static constexpr int MINB = min_blocks<N>();
 };
 
 __device__ __forceinline__ int signed_freq(int j, int n) { return j < (n >> 1) ? j : j - n; }
 
 // ---------------------------------------------------------------------------
-// Row pass: CTA = (wave, tile of ROWS rows).  blockIdx.x runs over the waves so
-// that consecutive CTAs read the same rows of t_n (kept in L2 for the batch).
+// Row pass: persistent CTAs over tiles of ROWS rows of one wave.  Tile index
+// runs over the waves fastest, so the CTAs active at any moment read the same
+// rows of t_n (kept in L2 for the whole batch).
 // ---------------------------------------------------------------------------
 template <int N, int MODE>
-__global__ void __launch_bounds__(RowCfg<N>::THREADS) k_row_pass(const PassArgs a) {
+__global__ void __launch_bounds__(RowCfg<N>::THREADS, RowCfg<N>::MINB) k_row_pass(const PassArgs a, int n_tiles) {
   using Cfg = RowCfg<N>;
   constexpr int E = Cfg::E, T = Cfg::T;
   extern __shared__ float2 smem[];
+  float2* tw = smem + Cfg::ROWS * Cfg::ROWBUF;
+  build_twiddles<N>(tw, threadIdx.x, Cfg::THREADS);
+  __syncthreads();
   const int t = threadIdx.x % T;
   const int rl = threadIdx.x / T;
-  const int wave = blockIdx.x;
-  const int row = blockIdx.y * Cfg::ROWS + rl;
-  float2* w = a.wave + (size_t)wave * N * N + (size_t)row * N;
   const SmemView<E, 1> view{smem + rl * Cfg::ROWBUF};
   auto sync = [] {
     if constexpr (T > 32 || Cfg::THREADS <= 32) __syncthreads();
     else __syncwarp();
   };
 
-  float2 v[E];
-  if constexpr (MODE == ROW_BEAM0) {
-    // plane wave exp(2 pi i (m x + n y) / N), argument reduced exactly in integers
-    const int2 mn = a.beams[wave];
+  for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    const int wave = tile % a.batch;
+    const int row = (tile / a.batch) * Cfg::ROWS + rl;
+    float2* w = a.wave + (size_t)wave * N * N + (size_t)row * N;
+
+    float2 v[E];
+    if constexpr (MODE == ROW_BEAM0) {
+      // plane wave exp(2 pi i (m x + n y) / N), argument reduced exactly in integers
+      const int2 mn = a.beams[wave];
 #pragma unroll
-    for (int q = 0; q < E; ++q) {
-      const int x = t + q * T;
-      const int k = (int)((((long long)mn.x * x + (long long)mn.y * row) % N + N) % N);
-      float s, c;
-      sincospif(2.0f * (float)k / (float)N, &s, &c);
-      v[q] = make_float2(c, s);
+      for (int q = 0; q < E; ++q) {
+        const int x = t + q * T;
+        const int k = (int)((((long long)mn.x * x + (long long)mn.y * row) % N + N) % N);
+        float s, c;
+        sincospif(2.0f * (float)k / (float)N, &s, &c);
+        v[q] = make_float2(c, s);
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < E; ++q) v[q] = w[t + q * T];
     }
-  } else {
-#pragma unroll
-    for (int q = 0; q < E; ++q) v[q] = w[t + q * T];
-  }
+#if STEM_PREFETCH
+    if constexpr (MODE != ROW_BEAM0) {
+      const int nt = tile + gridDim.x;
+      if (t == 0 && nt < n_tiles) {
+        const int nrow = (nt / a.batch) * Cfg::ROWS + rl;
+        prefetch_l2_bulk(a.wave + (size_t)(nt % a.batch) * N * N + (size_t)nrow * N, N * sizeof(float2));
+      }
+    }
+#endif
 
-  if constexpr (MODE == ROW_SLICE || MODE == ROW_IFFT_MAX || MODE == ROW_IFFT)
-    fft_dist<N, true>(v, view, t, sync);
+    if constexpr (MODE == ROW_SLICE || MODE == ROW_IFFT_MAX || MODE == ROW_IFFT)
+      fft_dist<N, true>(v, view, t, sync, tw);
 
-  if constexpr (MODE == ROW_SLICE || MODE == ROW_BEAM0) {
-    const float2* tr = a.trans + (size_t)row * N;
+    if constexpr (MODE == ROW_SLICE || MODE == ROW_BEAM0) {
+      const float2* tr = a.trans + (size_t)row * N;
 #pragma unroll
-    for (int q = 0; q < E; ++q) v[q] = cmul(v[q], __ldg(tr + t + q * T));
-  }
+      for (int q = 0; q < E; ++q) v[q] = cmul(v[q], __ldg(tr + t + q * T));
+    }
 
-  if constexpr (MODE == ROW_SLICE || MODE == ROW_BEAM0 || MODE == ROW_FFT)
-    fft_dist<N, false>(v, view, t, sync);
+    if constexpr (MODE == ROW_SLICE || MODE == ROW_BEAM0 || MODE == ROW_FFT)
+      fft_dist<N, false>(v, view, t, sync, tw);
 
 #pragma unroll
-  for (int q = 0; q < E; ++q) w[t + q * T] = v[q];
+    for (int q = 0; q < E; ++q) w[t + q * T] = v[q];
 
-  if constexpr (MODE == ROW_IFFT_MAX) {
-    float m = 0.0f;
+    if constexpr (MODE == ROW_IFFT_MAX) {
+      float m = 0.0f;
 #pragma unroll
-    for (int q = 0; q < E; ++q) m = fmaxf(m, fmaxf(fabsf(v[q].x), fabsf(v[q].y)));
+      for (int q = 0; q < E; ++q) m = fmaxf(m, fmaxf(fabsf(v[q].x), fabsf(v[q].y)));
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if ((threadIdx.x & 31) == 0) atomicMax(a.beam_max + wave, __float_as_uint(m));
+      for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+      if ((threadIdx.x & 31) == 0) atomicMax(a.beam_max + wave, __float_as_uint(m));
+    }
   }
 }
 
 // ---------------------------------------------------------------------------
-// Column pass: CTA = (tile of C columns, wave).  Thread (c, t) = threadIdx
-// c + C t holds column elements t + T q; neighbouring lanes read neighbouring
-// columns, so every global access is C * 8 contiguous bytes.
+// Column pass: persistent CTAs over tiles of C columns of one wave.  Thread
+// (c, t) = threadIdx c + C t holds column elements t + T q; neighbouring lanes
+// read neighbouring columns, so every global access is C * 8 contiguous bytes.
 // ---------------------------------------------------------------------------
 template <int N, int MODE>
-__global__ void __launch_bounds__(ColCfg<N>::THREADS) k_col_pass(const PassArgs a) {
+__global__ void __launch_bounds__(ColCfg<N>::THREADS, ColCfg<N>::MINB) k_col_pass(const PassArgs a, int n_tiles) {
   using Cfg = ColCfg<N>;
   constexpr int E = Cfg::E, T = Cfg::T, C = Cfg::C;
   extern __shared__ float2 smem[];
+  float2* tw = smem + (N + N / E) * C;
+  float* ring_acc = reinterpret_cast<float*>(tw + TwLayout<N>::TOTAL);
+  build_twiddles<N>(tw, threadIdx.x, Cfg::THREADS);
+  __syncthreads();
   const int c = threadIdx.x % C;
   const int t = threadIdx.x / C;
-  const int col = blockIdx.x * C + c;
-  const int wave = blockIdx.y;
-  float2* w = a.wave + (size_t)wave * N * N + col;
   const SmemView<E, C> view{smem + c};
   auto sync = [] { __syncthreads(); };
-  float* ring_acc = reinterpret_cast<float*>(smem + (N + N / E) * C);
+  constexpr int col_tiles = N / C;
 
-  if constexpr (MODE == COL_DET) {
-    for (int i = threadIdx.x; i < a.n_rings; i += Cfg::THREADS) ring_acc[i] = 0.0f;
-  }
+  for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    const int wave = tile / col_tiles;
+    const int col = (tile % col_tiles) * C + c;
+    float2* w = a.wave + (size_t)wave * N * N + col;
 
-  float2 v[E];
-  if constexpr (MODE == COL_PROBE_INIT) {
-    // psi_hat(m, n) = A(m, n) exp(-2 pi i (m x_p / Lx + n y_p / Ly)) / (sqrt|A| N^2);
-    // the phase is reduced in FP64, then evaluated in FP32.
-    const double xp = a.probe_xy[2 * wave], yp = a.probe_xy[2 * wave + 1];
-    const double thx = (double)signed_freq(col, N) * xp * a.inv_lx;
+    if constexpr (MODE == COL_DET) {
+      __syncthreads();   // the previous tile's flush has read ring_acc
+      for (int i = threadIdx.x; i < a.n_rings; i += Cfg::THREADS) ring_acc[i] = 0.0f;
+    }
+
+    float2 v[E];
+    if constexpr (MODE == COL_PROBE_INIT) {
+      // psi_hat(m, n) = A(m, n) exp(-2 pi i (m x_p / Lx + n y_p / Ly)) / (sqrt|A| N^2);
+      // the phase is reduced in FP64, then evaluated in FP32.
+      const double xp = a.probe_xy[2 * wave], yp = a.probe_xy[2 * wave + 1];
+      const double thx = (double)signed_freq(col, N) * xp * a.inv_lx;
 #pragma unroll
-    for (int q = 0; q < E; ++q) {
-      const int ky = t + q * T;
-      const uint16_t l = __ldg(a.lut + (size_t)ky * N + col);
-      float2 val = make_float2(0.0f, 0.0f);
-      if (l & kLutAperture) {
-        double th = thx + (double)signed_freq(ky, N) * yp * a.inv_ly;
-        th -= rint(th);
-        float s, cth;
-        sincospif(-2.0f * (float)th, &s, &cth);
-        val = make_float2(cth * a.probe_norm, s * a.probe_norm);
+      for (int q = 0; q < E; ++q) {
+        const int ky = t + q * T;
+        const uint16_t l = __ldg(a.lut + (size_t)ky * N + col);
+        float2 val = make_float2(0.0f, 0.0f);
+        if (l & kLutAperture) {
+          double th = thx + (double)signed_freq(ky, N) * yp * a.inv_ly;
+          th -= rint(th);
+          float s, cth;
+          sincospif(-2.0f * (float)th, &s, &cth);
+          val = make_float2(cth * a.probe_norm, s * a.probe_norm);
+        }
+        v[q] = val;
       }
-      v[q] = val;
-    }
-  } else {
+    } else {
 #pragma unroll
-    for (int q = 0; q < E; ++q) v[q] = w[(size_t)(t + q * T) * N];
-  }
-
-  if constexpr (MODE == COL_SLICE || MODE == COL_DET || MODE == COL_FFT)
-    fft_dist<N, false>(v, view, t, sync);
-
-  if constexpr (MODE == COL_SLICE) {
-    const int m = signed_freq(col, N);
-    const float2 px = cscale(__ldg(a.prop_x + col), a.prop_scale);
-#pragma unroll
-    for (int q = 0; q < E; ++q) {
-      const int ky = t + q * T;
-      const int n = signed_freq(ky, N);
-      const bool keep = 9 * (m * m + n * n) <= N * N;
-      v[q] = keep ? cmul(v[q], cmul(px, __ldg(a.prop_y + ky))) : make_float2(0.0f, 0.0f);
+      for (int q = 0; q < E; ++q) v[q] = w[(size_t)(t + q * T) * N];
     }
-  }
-
-  if constexpr (MODE == COL_SLICE || MODE == COL_PROBE_INIT || MODE == COL_IFFT)
-    fft_dist<N, true>(v, view, t, sync);
-
-  if constexpr (MODE == COL_DET) {
-    __syncthreads();   // ring_acc zeroed
+#if STEM_PREFETCH
+    if constexpr (MODE != COL_PROBE_INIT) {
+      // one prefetch per 32-byte sector of the next tile's column strip
+      const int nt = tile + gridDim.x;
+      if (nt < n_tiles && (c % (C < 4 ? C : 4)) == 0) {
+        const float2* nw = a.wave + (size_t)(nt / col_tiles) * N * N + (nt % col_tiles) * C + c;
 #pragma unroll
-    for (int q = 0; q < E; ++q) {
-      const int ky = t + q * T;
-      const int r = __ldg(a.lut + (size_t)ky * N + col) & kLutNoRing;
-      if (r != kLutNoRing) atomicAdd(ring_acc + r, cabs2(v[q]));
+        for (int q = 0; q < E; ++q) prefetch_l2(nw + (size_t)(t + q * T) * N);
+      }
     }
-    __syncthreads();
-    float* out = a.rings + (size_t)wave * a.n_rings;
-    for (int i = threadIdx.x; i < a.n_rings; i += Cfg::THREADS) {
-      const float acc = ring_acc[i];
-      if (acc != 0.0f) atomicAdd(out + i, acc * a.ring_scale);
-    }
-  } else {
+#endif
+
+    if constexpr (MODE == COL_SLICE || MODE == COL_DET || MODE == COL_FFT)
+      fft_dist<N, false>(v, view, t, sync, tw);
+
+    if constexpr (MODE == COL_SLICE) {
+      const int m = signed_freq(col, N);
+      const float2 px = cscale(__ldg(a.prop_x + col), a.prop_scale);
 #pragma unroll
-    for (int q = 0; q < E; ++q) w[(size_t)(t + q * T) * N] = v[q];
+      for (int q = 0; q < E; ++q) {
+        const int ky = t + q * T;
+        const int n = signed_freq(ky, N);
+        const bool keep = 9 * (m * m + n * n) <= N * N;
+        v[q] = keep ? cmul(v[q], cmul(px, __ldg(a.prop_y + ky))) : make_float2(0.0f, 0.0f);
+      }
+    }
+
+    if constexpr (MODE == COL_SLICE || MODE == COL_PROBE_INIT || MODE == COL_IFFT)
+      fft_dist<N, true>(v, view, t, sync, tw);
+
+    if constexpr (MODE == COL_DET) {
+      __syncthreads();   // ring_acc zeroed
+#pragma unroll
+      for (int q = 0; q < E; ++q) {
+        const int ky = t + q * T;
+        const int r = __ldg(a.lut + (size_t)ky * N + col) & kLutNoRing;
+        if (r != kLutNoRing) atomicAdd(ring_acc + r, cabs2(v[q]));
+      }
+      __syncthreads();
+      float* out = a.rings + (size_t)wave * a.n_rings;
+      for (int i = threadIdx.x; i < a.n_rings; i += Cfg::THREADS) {
+        const float acc = ring_acc[i];
+        if (acc != 0.0f) atomicAdd(out + i, acc * a.ring_scale);
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < E; ++q) w[(size_t)(t + q * T) * N] = v[q];
+    }
   }
 }
 
@@ -196,14 +264,30 @@ static cudaError_t set_smem(K kernel, size_t bytes, std::once_flag& flag) {
   return err;
 }
 
+// Persistent grid: as many CTAs as fit on the device at once, capped by the
+// number of tiles.
+template <class K>
+static int resident_ctas(K kernel, int threads, size_t smem, std::once_flag& flag, int& cached) {
+  std::call_once(flag, [&] {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, smem);
+    cached = (sms > 0 ? sms : 148) * (per > 0 ? per : 1);
+  });
+  return cached;
+}
+
 template <int N, int MODE>
 static cudaError_t row_launch(const PassArgs& a, cudaStream_t s) {
   using Cfg = RowCfg<N>;
-  static std::once_flag flag;
+  static std::once_flag flag, occ_flag;
+  static int occ = 0;
   cudaError_t e = set_smem(k_row_pass<N, MODE>, Cfg::SMEM, flag);
   if (e != cudaSuccess) return e;
-  dim3 grid(a.batch, N / Cfg::ROWS);
-  note_launch(), k_row_pass<N, MODE><<<grid, Cfg::THREADS, Cfg::SMEM, s>>>(a);
+  const int n_tiles = a.batch * (N / Cfg::ROWS);
+  const int grid = std::min(n_tiles, resident_ctas(k_row_pass<N, MODE>, Cfg::THREADS, Cfg::SMEM, occ_flag, occ));
+  note_launch(), k_row_pass<N, MODE><<<grid, Cfg::THREADS, Cfg::SMEM, s>>>(a, n_tiles);
   return cudaGetLastError();
 }
 
@@ -211,11 +295,13 @@ template <int N, int MODE>
 static cudaError_t col_launch(const PassArgs& a, cudaStream_t s) {
   using Cfg = ColCfg<N>;
   const size_t smem = Cfg::FFT_SMEM + (MODE == COL_DET ? kMaxRings * sizeof(float) : 0);
-  static std::once_flag flag;
-  cudaError_t e = set_smem(k_col_pass<N, MODE>, Cfg::FFT_SMEM + kMaxRings * sizeof(float), flag);
+  static std::once_flag flag, occ_flag;
+  static int occ = 0;
+  cudaError_t e = set_smem(k_col_pass<N, MODE>, smem, flag);
   if (e != cudaSuccess) return e;
-  dim3 grid(N / Cfg::C, a.batch);
-  note_launch(), k_col_pass<N, MODE><<<grid, Cfg::THREADS, smem, s>>>(a);
+  const int n_tiles = a.batch * (N / Cfg::C);
+  const int grid = std::min(n_tiles, resident_ctas(k_col_pass<N, MODE>, Cfg::THREADS, smem, occ_flag, occ));
+  note_launch(), k_col_pass<N, MODE><<<grid, Cfg::THREADS, smem, s>>>(a, n_tiles);
   return cudaGetLastError();
 }
 

@@ -100,6 +100,11 @@ void stem_plan_destroy(stem_plan plan);
 stem_status stem_plan_constants(stem_plan plan, double* lambda_a, double* sigma,
                                 int32_t* n_aperture);
 
+/* Device status word of the plan: kernels whose waits are bounded (the
+ * tensor-core beam sum) record STEM_ERR_TIMEOUT there instead of hanging.
+ * Copies it to *code (host) and clears it; synchronous (waits for the copy). */
+stem_status stem_plan_device_status(stem_plan plan, int32_t* code);
+
 /* ---------------------------------------------------------------------------
  * Projected potentials (Methods, "Calculation of the Projected Potentials").
  * The paper's Kirkland look-up table is replaced by a sum of two isotropic

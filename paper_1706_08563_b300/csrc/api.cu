@@ -95,6 +95,7 @@ const char* stem_status_string(stem_status s) {
 
 void stem_plan_destroy(stem_plan pl) {
   if (!pl) return;
+  cudaFree(pl->status);
   cudaFree(pl->prop_x);
   cudaFree(pl->prop_y);
   for (int i = 0; i <= kMaxLog2F; ++i) {
@@ -161,6 +162,8 @@ stem_status stem_plan_create(const stem_params* params, stem_plan* out) {
     e = cudaMalloc(dst, bytes > 0 ? bytes : 16);
     if (e == cudaSuccess && bytes > 0) e = cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice);
   };
+  const int zero = 0;
+  upload(reinterpret_cast<void**>(&pl->status), &zero, sizeof(int));
   upload(reinterpret_cast<void**>(&pl->prop_x), px.data(), n * sizeof(float2));
   upload(reinterpret_cast<void**>(&pl->prop_y), py.data(), n * sizeof(float2));
 
@@ -196,6 +199,16 @@ stem_status stem_plan_create(const stem_params* params, stem_plan* out) {
     return e == cudaErrorMemoryAllocation ? STEM_ERR_NOMEM : STEM_ERR_CUDA;
   }
   *out = pl;
+  return STEM_OK;
+}
+
+stem_status stem_plan_device_status(stem_plan pl, int32_t* code) {
+  if (!pl || !code) return STEM_ERR_INVALID;
+  int v = 0;
+  if (cudaMemcpy(&v, pl->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return STEM_ERR_CUDA;
+  const int zero = 0;
+  if (v != 0 && cudaMemcpy(pl->status, &zero, sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess) return STEM_ERR_CUDA;
+  *code = v;
   return STEM_OK;
 }
 
@@ -348,7 +361,8 @@ static stem_status output_common(stem_plan pl, int32_t f, stem_storage storage, 
   o.w = pl->n / f;
   o.storage = storage;
   o.engine = engine == STEM_SUM_AUTO ? STEM_SUM_SIMT : engine;
-  if (o.engine == STEM_SUM_TENSOR) return STEM_ERR_UNSUPPORTED;
+  if (o.engine == STEM_SUM_TENSOR && storage == STEM_F32) return STEM_ERR_UNSUPPORTED;
+  o.status = pl->status;
   o.n_beams = L.n_beams;
   o.nbp = L.nbp;
   o.beams = pl->beams[lf];

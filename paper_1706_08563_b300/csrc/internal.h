@@ -77,7 +77,15 @@ struct OutputArgs {
   const void* sdata = nullptr;
   double lx = 0, ly = 0, dx = 0, dy = 0;
   float coef_norm = 0.0f;
+  int* status = nullptr;    // plan's device status word (bounded waits record timeouts here)
 };
+// tcgen05 beam sum (umma.cu)
+int umma_group();
+size_t umma_smem_bytes();
+cudaError_t launch_beam_sum_umma(const OutputArgs& o, int np, const double* probe_xy, void* coef, const int2* origin,
+                                 const int* offsets, const int* work, const int* list, int n_tiles, float2* windows,
+                                 cudaStream_t s);
+
 cudaError_t prism_windows_chunk(const OutputArgs& o, const double* probe_xy, int np, float2* windows,
                                 char* ws, const OutputWs& L, cudaStream_t s);
 
@@ -100,4 +108,5 @@ struct stem_plan_s {
   int2* beams[stem::kMaxLog2F + 1] = {};
   int n_beams[stem::kMaxLog2F + 1] = {};
   std::vector<int2> h_beams[stem::kMaxLog2F + 1];
+  int* status = nullptr;   // device status word, 0 = ok
 };

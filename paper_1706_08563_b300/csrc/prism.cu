@@ -363,20 +363,25 @@ cudaError_t prism_windows_chunk(const OutputArgs& o, const double* probe_xy, int
   int* list = reinterpret_cast<int*>(ws + L.list);
   const int n = o.n, w = o.w;
   const int n_tiles = (n / kTileX) * (n / kTileY);
+  const bool tensor = o.engine == STEM_SUM_TENSOR;
+  const int group = tensor ? umma_group() : kGroup;
   cudaError_t e;
 
   dim3 cg((o.nbp + 127) / 128, np);
-  note_launch(), k_coefficients<<<cg, 128, 0, s>>>(probe_xy, o.beams, o.n_beams, o.nbp, o.scales, 1.0 / o.lx, 1.0 / o.ly,
-                                    o.coef_norm, coef);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (!tensor) {
+    note_launch(), k_coefficients<<<cg, 128, 0, s>>>(probe_xy, o.beams, o.n_beams, o.nbp, o.scales, 1.0 / o.lx,
+                                                    1.0 / o.ly, o.coef_norm, coef);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
   if ((e = cudaMemsetAsync(counts, 0, n_tiles * sizeof(int), s)) != cudaSuccess) return e;
   note_launch(), k_origins<<<(np + 127) / 128, 128, 0, s>>>(probe_xy, np, n, w, o.dx, o.dy, origin, counts);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  note_launch(), k_scan_tiles<<<1, 1024, 0, s>>>(counts, n_tiles, kGroup, offsets, work);
+  note_launch(), k_scan_tiles<<<1, 1024, 0, s>>>(counts, n_tiles, group, offsets, work);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   note_launch(), k_fill_tiles<<<(np + 127) / 128, 128, 0, s>>>(origin, np, n, w, offsets, counts, list);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
 
+  if (tensor) return launch_beam_sum_umma(o, np, probe_xy, coef, origin, offsets, work, list, n_tiles, windows, s);
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

@@ -281,3 +281,38 @@ def test_prism_free_space_closed_form(api):
         if r >= 0:
             counts[r] += 1
     assert np.max(np.abs(got - counts[None] / len(beams))) <= 1e-5
+
+
+# ------------------------------------------------------- tensor-core beam sum
+def _device_status(plan):
+    import ctypes
+    from paper_1706_08563_b300 import _lib
+    code = ctypes.c_int32(-99)
+    assert _lib.load().stem_plan_device_status(plan._h, ctypes.byref(code)) == _lib.STEM_OK
+    return code.value
+
+
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+@pytest.mark.parametrize("n,f", [(128, 4), (256, 2)])
+def test_prism_tensor_engine_vs_simt_and_oracle(api, storage, n, f):
+    """tcgen05 complex GEMM beam sum: same windows as the CUDA-core engine on the
+    same 16-bit S-matrix (both accumulate in FP32), and rings within the
+    reduced-precision bound of the FP64 oracle."""
+    w, xyz, gauss = _small_prism_case(n=n, f=f)
+    plan = api.Plan.from_workload(w)
+    p, tref = _oracle_trans(w, xyz, gauss)
+    beams = O.prism_beams(p, f)
+    sm = plan.prism_smatrix(dev(tref, torch.complex64), f, storage, batch=32)
+    xy = np.concatenate([W.scan_positions(w, scan=7), W.random_positions(w, 150, seed=3)])
+    d_xy = dev(xy)
+    wt = plan.prism_windows(sm, d_xy, engine="tensor").cpu().numpy()
+    ws = plan.prism_windows(sm, d_xy, engine="simt").cpu().numpy()
+    assert _device_status(plan) == 0
+    # both engines multiply 16-bit operands exactly and sum in FP32; the tensor
+    # engine also rounds the coefficients to 16 bits
+    eps = 2.0 ** -11 if storage == "f16" else 2.0 ** -8
+    assert np.linalg.norm(wt - ws) / np.linalg.norm(ws) <= 4 * eps
+    got = plan.prism_output(sm, d_xy, chunk=100, engine="tensor").cpu().numpy()
+    ref = O.prism_rings(p, O.prism_smatrix(p, tref, beams), beams, f, xy)
+    check_rings(got, ref, LOWP_TOL)
+    assert _device_status(plan) == 0

@@ -232,7 +232,7 @@ def run_ours(args, rank, world, local_rank):
            "step": "potentials + " + ("S-matrix + PRISM output" if prism else "multislice scan")}
     if prism:
         cfg.update({"f": f, "beams": n_beams, "smatrix_storage": args.storage, "chunk": chunk,
-                    "beam_sum": "FP32 CUDA cores"})
+                    "beam_sum": "FP32 CUDA cores" if args.storage == "f32" else "tcgen05 complex GEMM (16-bit in, FP32 accumulate)"})
     res["config"] = cfg
     res["phases_ms"] = {"potentials": statistics.mean(pot_ms),
                         ("smatrix" if prism else "unused"): statistics.mean(sm_ms),

@@ -360,7 +360,7 @@ static stem_status output_common(stem_plan pl, int32_t f, stem_storage storage, 
   o.f = f;
   o.w = pl->n / f;
   o.storage = storage;
-  o.engine = engine == STEM_SUM_AUTO ? STEM_SUM_SIMT : engine;
+  o.engine = engine == STEM_SUM_AUTO ? (storage == STEM_F32 ? STEM_SUM_SIMT : STEM_SUM_TENSOR) : engine;
   if (o.engine == STEM_SUM_TENSOR && storage == STEM_F32) return STEM_ERR_UNSUPPORTED;
   o.status = pl->status;
   o.n_beams = L.n_beams;

@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--workload", default=W.C4.name, choices=sorted(W.WORKLOADS))
     ap.add_argument("--storage", default="f16", choices=["f32", "f16", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
     return ap.parse_args()
 
 
@@ -269,6 +270,8 @@ def run_ours(args, rank, world, local_rank):
     res["wall_s_timed"] = wall
     if prism and rank == 0:
         res["multislice"] = measure_multislice(args, dev, hbm, src)
+    if rank == 0 and not args.no_serving:
+        res["serving"] = measure_serving(dev)
     return res
 
 
@@ -306,6 +309,69 @@ def measure_multislice(args, dev, hbm, src):
             "batch": w.batch, "grid": w.n, "slices": w.n_slices,
             "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
                          "peak_source": src, "kernel": "k_row_pass/k_col_pass<1024>"}}
+
+
+def measure_serving(dev, n_requests=40, rate_hz=40.0):
+    """Seeded Poisson stream of mixed multislice / PRISM requests through the
+    continuous-batching server, against the same requests run one at a time."""
+    import threading
+    import torch
+    from paper_1706_08563_b300.serve import Server, SimRequest, run_serial
+    recipes = W.serving_recipes()
+    atoms = {r.specimen: W.atoms(r.workload, seed=r.seed) for r in recipes}
+    stream = W.serving_requests(recipes, n_requests, rate_hz)
+
+    def make(k, xy):
+        r = recipes[k]
+        xyz, gauss = atoms[r.specimen]
+        return SimRequest(r.specimen, r.workload, xyz, gauss, xy, r.algo, r.f, r.storage)
+
+    reqs = [make(k, xy) for _, k, xy in stream]
+    probes = sum(r.probe_xy.shape[0] for r in reqs)
+    run_serial(reqs[:3], device=dev)                 # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    run_serial(reqs, device=dev)
+    torch.cuda.synchronize()
+    t_serial = time.perf_counter() - t0
+    # latency: Poisson arrivals, results as soon as their probes are done
+    srv = Server(64 << 30, batch=64, prism_chunk=1024, arena=8192, device=dev)
+    srv.start()
+    futs = []
+    t_start = time.perf_counter()
+
+    def feeder():
+        for (t_arr, k, xy), r in zip(stream, reqs):
+            delay = t_start + t_arr - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            futs.append(srv.submit(r))
+    th = threading.Thread(target=feeder)
+    th.start()
+    th.join()
+    for fu in futs:
+        fu.result(timeout=600)
+    srv.stop()
+    lat = np.array(srv.latencies) * 1e3
+    # capacity: the same requests queued at once (fresh server, no resident lanes)
+    burst = [make(k, xy) for _, k, xy in stream]
+    srv2 = Server(64 << 30, batch=64, prism_chunk=1024, arena=8192, device=dev)
+    futs2 = [srv2.submit(r) for r in burst]
+    t0 = time.perf_counter()
+    srv2.start()
+    for fu in futs2:
+        fu.result(timeout=600)
+    t_burst = time.perf_counter() - t0
+    srv2.stop()
+    return {"requests": n_requests, "probes": probes, "arrival_rate_hz": rate_hz,
+            "recipes": [f"{r.algo} N={r.workload.n} S={r.workload.n_slices}" + (f" f={r.f} {r.storage}" if r.algo == "prism" else "")
+                        for r in recipes],
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "burst_probes_s": probes / t_burst, "serial_probes_s": probes / t_serial,
+            "speedup_vs_serial": t_serial / t_burst, "launches_poisson": srv.launches, "launches_burst": srv2.launches,
+            "what": ("p50/p99: arrival to result on the host under Poisson arrivals; burst: all requests queued at "
+                     "once through the server; serial: the same requests one at a time, no overlap, no resident "
+                     "potentials")}
 
 
 # --------------------------------------------------------------------------- oracle

@@ -160,3 +160,52 @@ def serving_stream(n_requests: int, rate_hz: float, seed: int = ARRIVAL_SEED,
                      scan, 1.0, 100)
         out.append(Request(i, t, kind, w, f))
     return out
+
+
+@dataclasses.dataclass
+class Recipe:
+    """A specimen plus fixed simulation settings that several requests share."""
+    specimen: str
+    workload: Workload
+    algo: str
+    f: int
+    storage: str
+    seed: int
+
+
+def serving_recipes(grids: Tuple[int, ...] = (256, 512), cell: float = 50.0, n_atoms: int = 6000,
+                    seed: int = ARRIVAL_SEED, count: int = 6) -> List[Recipe]:
+    """Seeded mix of multislice and PRISM settings (grid, slice count, f, storage)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        n = int(rng.choice(grids))
+        slices = int(rng.integers(10, 41))
+        algo = "prism" if i % 2 else "ms"
+        f = int(rng.choice((4, 8, 16))) if algo == "prism" else 1
+        storage = str(rng.choice(("f16", "bf16", "f32"))) if algo == "prism" else "f32"
+        w = Workload(f"spec{i}", (cell, cell, slices * 1.0), n_atoms * slices // 40, n, slices, 1.0, 200.0,
+                     20.0, 16, 1.0, 100)
+        out.append(Recipe(f"spec{i}", w, algo, f, storage, seed + 1 + i))
+    return out
+
+
+def serving_requests(recipes: List[Recipe], n_requests: int, rate_hz: float, seed: int = ARRIVAL_SEED,
+                     scans: Tuple[int, ...] = (8, 16, 32)):
+    """Poisson arrivals; each request scans a random square region of one recipe's
+    specimen.  Returns [(arrival_s, recipe_index, probe_xy float64 [P, 2])]."""
+    rng = np.random.default_rng(seed + 99)
+    t = 0.0
+    out = []
+    for _ in range(n_requests):
+        t += rng.exponential(1.0 / rate_hz)
+        k = int(rng.integers(len(recipes)))
+        w = recipes[k].workload
+        s = int(rng.choice(scans))
+        step = w.cell[0] / 64.0
+        x0, y0 = rng.random(2) * np.asarray(w.cell[:2])
+        g = np.arange(s) * step
+        yy, xx = np.meshgrid(y0 + g, x0 + g, indexing="ij")
+        xy = np.stack([np.mod(xx.ravel(), w.cell[0]), np.mod(yy.ravel(), w.cell[1])], axis=1)
+        out.append((t, k, xy))
+    return out

@@ -242,20 +242,24 @@ def run_ours(args, rank, world, local_rank):
                       "what": "one whole simulation (device time)"}
     hbm, _, src = peaks()
     n2 = w.n * w.n
+    # inside the slice loop only the columns within the 2/3 band limit hold data
+    band = (2 * (w.n // 3) + 1) / w.n
     if prism:
         nbatches = math.ceil(n_beams / batch)
         # row + column pass per beam and slice: read + write of the wave each; t_n once per batch
         esz = 4 if args.storage == "f32" else 2
-        # per beam: 2 HBM round trips per slice (row + column pass), the final row
-        # IFFT pass and the transposing store; t_n is read once per beam batch
-        alg = n_beams * (w.n_slices * 32.0 + 16.0 + 2.0 * esz) * n2 + nbatches * w.n_slices * 8.0 * n2
+        # per beam: 2 HBM round trips per slice (row + column pass) over the in-band
+        # columns, the final row IFFT pass (in-band read, full write) and the
+        # transposing store; t_n is read once per beam batch
+        alg = (n_beams * (w.n_slices * 32.0 * band + 8.0 * band + 8.0 + 8.0 + 2.0 * esz) * n2
+               + nbatches * w.n_slices * 8.0 * n2)
         ms = statistics.mean(sm_ms)
         kernel = f"k_row_pass/k_col_pass<{w.n}> (S-matrix slice passes)"
     else:
         nb = math.ceil(n_probes / batch)
-        # per probe: init write (8 B), then per slice row + column pass (32 B), the
-        # last column pass reads only (detector): 32 S B per pixel; t_n once per batch
-        alg = n_probes * w.n_slices * 32.0 * n2 + nb * w.n_slices * 8.0 * n2
+        # per probe: init write, then per slice row + column pass, the last column
+        # pass reads only (detector): 32 S B per in-band pixel; t_n once per batch
+        alg = n_probes * w.n_slices * 32.0 * band * n2 + nb * w.n_slices * 8.0 * n2
         ms = statistics.mean(out_ms)
         kernel = f"k_row_pass/k_col_pass<{w.n}> (multislice slice passes)"
     ach = alg / (ms / 1e3) / 1e9
@@ -303,7 +307,8 @@ def measure_multislice(args, dev, hbm, src):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / k
     n2 = w.n * w.n
-    alg = w.batch * w.n_slices * 32.0 * n2 + w.n_slices * 8.0 * n2
+    band = (2 * (w.n // 3) + 1) / w.n
+    alg = w.batch * w.n_slices * 32.0 * band * n2 + w.n_slices * 8.0 * n2
     ach = alg / (ms / 1e3) / 1e9
     return {"workload": w.name, "value": w.batch / (ms / 1e3), "unit": "probes/s", "ms_per_launch": ms,
             "batch": w.batch, "grid": w.n, "slices": w.n_slices,

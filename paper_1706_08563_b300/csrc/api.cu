@@ -264,6 +264,7 @@ stem_status stem_multislice_scan(stem_plan pl, const void* trans, const double* 
   a.inv_lx = 1.0 / pl->p.cell[0];
   a.inv_ly = 1.0 / pl->p.cell[1];
   a.probe_norm = (float)(1.0 / (std::sqrt((double)std::max(pl->n_aperture, 1)) * (double)plane));
+  a.band = 1;   // the last column pass reads waves whose out-of-band columns were never written
   const float2* t = static_cast<const float2*>(trans);
   for (int64_t p0 = 0; p0 < n_probes; p0 += batch) {
     a.batch = (int)std::min<int64_t>(batch, n_probes - p0);

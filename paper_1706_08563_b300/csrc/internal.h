@@ -33,6 +33,7 @@ struct PassArgs {
   float probe_norm = 0.0f;           // 1 / (sqrt(|A|) N^2)
   const int2* beams = nullptr;       // [batch] (m, n) (offset)
   unsigned* beam_max = nullptr;      // [batch] float bits of max(|Re|, |Im|)
+  int band = 0;                      // COL_DET ends a slice loop: only in-band columns hold data
 };
 
 enum RowMode { ROW_SLICE = 0, ROW_BEAM0 = 1, ROW_IFFT_MAX = 2, ROW_FFT = 3, ROW_IFFT = 4 };

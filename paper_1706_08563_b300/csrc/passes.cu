@@ -64,7 +64,20 @@ template <int N> struct ColCfg {
   static constexpr int THREADS = C * T;
   static constexpr size_t FFT_SMEM = ((size_t)(N + N / E) * C + TwLayout<N>::TOTAL) * sizeof(float2);
   static constexpr int MINB = min_blocks<N>();
+  // Column tiles inside the 2/3 band limit, |m| <= N/3 (columns [0, MB] and
+  // [N - MB, N)).  Outside it the propagator's mask zeroes whole columns, so
+  // the slice loop never reads or writes them.
+  static constexpr int MB = N / 3;
+  static constexpr int LO = (MB + 1 + C - 1) / C;     // tiles covering columns 0..MB
+  static constexpr int HI0 = (N - MB) / C;            // first tile touching columns N-MB..N-1
+  static constexpr bool SKIP = LO < HI0;
+  static constexpr int BAND_TILES = SKIP ? LO + N / C - HI0 : N / C;
+  __device__ static int band_tile(int k) { return (SKIP && k >= LO) ? k - LO + HI0 : k; }
 };
+
+// Is FFT column index x inside the 2/3 band limit (|m| <= N/3)?
+template <int N>
+__device__ __forceinline__ bool in_band(int x) { return x <= N / 3 || x >= N - N / 3; }
 
 __device__ __forceinline__ int signed_freq(int j, int n) { return j < (n >> 1) ? j : j - n; }
 
@@ -94,6 +107,10 @@ __global__ void __launch_bounds__(RowCfg<N>::THREADS, RowCfg<N>::MINB) k_row_pas
     const int row = (tile / a.batch) * Cfg::ROWS + rl;
     float2* w = a.wave + (size_t)wave * N * N + (size_t)row * N;
 
+    // slice-loop rows in the (k_x, y) domain hold zeros outside the band limit:
+    // they are neither read from nor written to memory
+    constexpr bool BAND_IN = MODE == ROW_SLICE || MODE == ROW_IFFT_MAX;
+    constexpr bool BAND_OUT = MODE == ROW_SLICE || MODE == ROW_BEAM0;
     float2 v[E];
     if constexpr (MODE == ROW_BEAM0) {
       // plane wave exp(2 pi i (m x + n y) / N), argument reduced exactly in integers
@@ -108,14 +125,25 @@ __global__ void __launch_bounds__(RowCfg<N>::THREADS, RowCfg<N>::MINB) k_row_pas
       }
     } else {
 #pragma unroll
-      for (int q = 0; q < E; ++q) v[q] = w[t + q * T];
+      for (int q = 0; q < E; ++q) {
+        const int x = t + q * T;
+        v[q] = (!BAND_IN || in_band<N>(x)) ? w[x] : make_float2(0.0f, 0.0f);
+      }
     }
 #if STEM_PREFETCH
     if constexpr (MODE != ROW_BEAM0) {
       const int nt = tile + gridDim.x;
       if (t == 0 && nt < n_tiles) {
         const int nrow = (nt / a.batch) * Cfg::ROWS + rl;
-        prefetch_l2_bulk(a.wave + (size_t)(nt % a.batch) * N * N + (size_t)nrow * N, N * sizeof(float2));
+        const float2* nr = a.wave + (size_t)(nt % a.batch) * N * N + (size_t)nrow * N;
+        if constexpr (BAND_IN) {
+          // the two in-band segments, widened to 16-byte boundaries
+          constexpr int lo = ((N / 3 + 1) + 1) & ~1, hi = (N - N / 3) & ~1;
+          prefetch_l2_bulk(nr, lo * sizeof(float2));
+          prefetch_l2_bulk(nr + hi, (N - hi) * sizeof(float2));
+        } else {
+          prefetch_l2_bulk(nr, N * sizeof(float2));
+        }
       }
     }
 #endif
@@ -133,7 +161,10 @@ __global__ void __launch_bounds__(RowCfg<N>::THREADS, RowCfg<N>::MINB) k_row_pas
       fft_dist<N, false>(v, view, t, sync, tw);
 
 #pragma unroll
-    for (int q = 0; q < E; ++q) w[t + q * T] = v[q];
+    for (int q = 0; q < E; ++q) {
+      const int x = t + q * T;
+      if (!BAND_OUT || in_band<N>(x)) w[x] = v[q];
+    }
 
     if constexpr (MODE == ROW_IFFT_MAX) {
       float m = 0.0f;
@@ -151,7 +182,7 @@ __global__ void __launch_bounds__(RowCfg<N>::THREADS, RowCfg<N>::MINB) k_row_pas
 // (c, t) = threadIdx c + C t holds column elements t + T q; neighbouring lanes
 // read neighbouring columns, so every global access is C * 8 contiguous bytes.
 // ---------------------------------------------------------------------------
-template <int N, int MODE>
+template <int N, int MODE, bool BAND>
 __global__ void __launch_bounds__(ColCfg<N>::THREADS, ColCfg<N>::MINB) k_col_pass(const PassArgs a, int n_tiles) {
   using Cfg = ColCfg<N>;
   constexpr int E = Cfg::E, T = Cfg::T, C = Cfg::C;
@@ -164,11 +195,12 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, ColCfg<N>::MINB) k_col_pas
   const int t = threadIdx.x / C;
   const SmemView<E, C> view{smem + c};
   auto sync = [] { __syncthreads(); };
-  constexpr int col_tiles = N / C;
+  constexpr int col_tiles = BAND ? Cfg::BAND_TILES : N / C;
 
   for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
     const int wave = tile / col_tiles;
-    const int col = (tile % col_tiles) * C + c;
+    const int ct = tile % col_tiles;
+    const int col = (BAND ? Cfg::band_tile(ct) : ct) * C + c;
     float2* w = a.wave + (size_t)wave * N * N + col;
 
     if constexpr (MODE == COL_DET) {
@@ -205,7 +237,8 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, ColCfg<N>::MINB) k_col_pas
       // one prefetch per 32-byte sector of the next tile's column strip
       const int nt = tile + gridDim.x;
       if (nt < n_tiles && (c % (C < 4 ? C : 4)) == 0) {
-        const float2* nw = a.wave + (size_t)(nt / col_tiles) * N * N + (nt % col_tiles) * C + c;
+        const int nct = nt % col_tiles;
+        const float2* nw = a.wave + (size_t)(nt / col_tiles) * N * N + (BAND ? Cfg::band_tile(nct) : nct) * C + c;
 #pragma unroll
         for (int q = 0; q < E; ++q) prefetch_l2(nw + (size_t)(t + q * T) * N);
       }
@@ -291,17 +324,17 @@ static cudaError_t row_launch(const PassArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-template <int N, int MODE>
+template <int N, int MODE, bool BAND>
 static cudaError_t col_launch(const PassArgs& a, cudaStream_t s) {
   using Cfg = ColCfg<N>;
   const size_t smem = Cfg::FFT_SMEM + (MODE == COL_DET ? kMaxRings * sizeof(float) : 0);
   static std::once_flag flag, occ_flag;
   static int occ = 0;
-  cudaError_t e = set_smem(k_col_pass<N, MODE>, smem, flag);
+  cudaError_t e = set_smem(k_col_pass<N, MODE, BAND>, smem, flag);
   if (e != cudaSuccess) return e;
-  const int n_tiles = a.batch * (N / Cfg::C);
-  const int grid = std::min(n_tiles, resident_ctas(k_col_pass<N, MODE>, Cfg::THREADS, smem, occ_flag, occ));
-  note_launch(), k_col_pass<N, MODE><<<grid, Cfg::THREADS, smem, s>>>(a, n_tiles);
+  const int n_tiles = a.batch * (BAND ? Cfg::BAND_TILES : N / Cfg::C);
+  const int grid = std::min(n_tiles, resident_ctas(k_col_pass<N, MODE, BAND>, Cfg::THREADS, smem, occ_flag, occ));
+  note_launch(), k_col_pass<N, MODE, BAND><<<grid, Cfg::THREADS, smem, s>>>(a, n_tiles);
   return cudaGetLastError();
 }
 
@@ -323,18 +356,21 @@ static cudaError_t row_dispatch(int mode, const PassArgs& a, cudaStream_t s) {
   return cudaErrorInvalidValue;
 }
 
+// Slice-loop column passes visit only the column tiles inside the band limit;
+// the detector pass does so when it ends a multislice run (a.band), not when
+// it reads PRISM windows or other full fields.
 template <int N>
 static cudaError_t col_dispatch(int mode, const PassArgs& a, cudaStream_t s) {
   switch (mode) {
-    case COL_DET: return col_launch<N, COL_DET>(a, s);
-    case COL_FFT: return col_launch<N, COL_FFT>(a, s);
-    case COL_IFFT: return col_launch<N, COL_IFFT>(a, s);
+    case COL_DET: return a.band ? col_launch<N, COL_DET, true>(a, s) : col_launch<N, COL_DET, false>(a, s);
+    case COL_FFT: return col_launch<N, COL_FFT, false>(a, s);
+    case COL_IFFT: return col_launch<N, COL_IFFT, false>(a, s);
     default: break;
   }
   if constexpr (N >= 64) {
     switch (mode) {
-      case COL_SLICE: return col_launch<N, COL_SLICE>(a, s);
-      case COL_PROBE_INIT: return col_launch<N, COL_PROBE_INIT>(a, s);
+      case COL_SLICE: return col_launch<N, COL_SLICE, true>(a, s);
+      case COL_PROBE_INIT: return col_launch<N, COL_PROBE_INIT, true>(a, s);
       default: break;
     }
   }

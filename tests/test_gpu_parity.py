@@ -142,7 +142,7 @@ def test_multislice_ragged_batches_and_weight(api):
     check_rings(many, ref, FP32_TOL)
 
 
-@pytest.mark.parametrize("n", [64, 256, 512])
+@pytest.mark.parametrize("n", [64, 256, 512, 1024, 2048])
 def test_multislice_sizes(api, n):
     w = W.Workload("t", (20.0, 24.0, 8.0), 30, n, 4, 2.0, 200.0, 25.0, 3, 2.0, 60)
     xyz, gauss = W.atoms(w, seed=n)
@@ -316,3 +316,25 @@ def test_prism_tensor_engine_vs_simt_and_oracle(api, storage, n, f):
     ref = O.prism_rings(p, O.prism_smatrix(p, tref, beams), beams, f, xy)
     check_rings(got, ref, LOWP_TOL)
     assert _device_status(plan) == 0
+
+
+@pytest.mark.parametrize("n,f,storage", [(1024, 8, "f32"), (1024, 4, "f16"), (2048, 16, "f32")])
+def test_prism_smatrix_tiled_sizes(api, n, f, storage):
+    """S-matrix at the sizes whose slice loop uses the 4-row tiled wave layout."""
+    w = W.Workload("p", (24.0, 24.0, 4.0), 40, n, 2, 2.0, 200.0, 20.0, 4, 2.0, 40, f=(f,))
+    xyz, gauss = W.atoms(w, seed=n + f)
+    plan = api.Plan.from_workload(w)
+    p, tref = _oracle_trans(w, xyz, gauss)
+    beams = O.prism_beams(p, f)
+    sm = plan.prism_smatrix(dev(tref, torch.complex64), f, storage, batch=5)
+    got = sm.beams_real_space().cpu().numpy()
+    pick = np.unique(np.linspace(0, len(beams) - 1, 4).astype(int))
+    ref = O.prism_smatrix(p, tref, beams[pick])
+    tol = 2e-5 if storage == "f32" else 2e-3
+    for k, b in enumerate(pick):
+        e = np.linalg.norm(got[b] - ref[k]) / np.linalg.norm(ref[k])
+        assert e <= tol, (b, e)
+    xy = W.random_positions(w, 6, seed=1)
+    out = plan.prism_output(sm, dev(xy)).cpu().numpy()
+    check_rings(out, O.prism_rings(p, O.prism_smatrix(p, tref, beams), beams, f, xy),
+                FP32_TOL if storage == "f32" else LOWP_TOL)

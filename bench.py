@@ -34,6 +34,9 @@ import numpy as np  # noqa: E402
 import workloads as W  # noqa: E402
 
 METRIC = "probes/s for multislice and PRISM f=8 at stated error; p50/p99 solve latency"
+# DRAM bytes per wave and slice (row + column pass, t_n excluded) from one ncu
+# capture of the current slice passes (profiles/slice_passes_dram_traffic.md)
+SLICE_TRAFFIC_PER_WAVE = {2048: 82.8e6, 1024: 19.8e6}
 HBM_FALLBACK_GBS = 6400.0
 
 
@@ -263,9 +266,13 @@ def run_ours(args, rank, world, local_rank):
         ms = statistics.mean(out_ms)
         kernel = f"k_row_pass/k_col_pass<{w.n}> (multislice slice passes)"
     ach = alg / (ms / 1e3) / 1e9
+    per_wave = SLICE_TRAFFIC_PER_WAVE.get(w.n)
+    waves = n_beams if prism else n_probes
+    batches = math.ceil(n_beams / batch) if prism else math.ceil(n_probes / batch)
+    traffic = None if per_wave is None else per_wave * waves * w.n_slices + batches * w.n_slices * 8.0 * n2
     res["roofline"] = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                       "traffic": None, "kernel": kernel, "peak_source": src,
-                       "algorithmic_bytes_per_step": alg}
+                       "traffic": traffic, "traffic_unit": "bytes per step (slice passes, scaled from a 16-wave capture)",
+                       "kernel": kernel, "peak_source": src, "algorithmic_bytes_per_step": alg}
     res["e2e"] = {"value": probes_all / (tot_e2e / 1e3), "unit": "probes/s",
                   "h2d_bytes_per_step": int(h_xyz.numel() * 8 + h_gauss.numel() * 4 + h_xy.numel() * 8),
                   "d2h_bytes_per_step": int(h_rings.numel() * 4)}

@@ -71,7 +71,13 @@ typedef enum {
  *   energy_kev beam energy; lambda and sigma are the relativistic values
  *   alpha_mrad probe convergence semi-angle (aperture: lambda |k| <= alpha)
  *   ring_width_mrad, n_rings  ring i collects lambda |k| in [i, i+1) * width,
- *              1 <= n_rings <= 2048, inside the 2/3 band limit 9 (m^2+n^2) <= N^2 */
+ *              1 <= n_rings <= 2048, inside the 2/3 band limit 9 (m^2+n^2) <= N^2
+ *   defocus_a, cs_a  probe aberrations C1 and Cs in Angstrom ("Description of
+ *              Algorithms": the probe coefficients carry the coherent wave
+ *              aberrations); the probe's Fourier coefficients and the PRISM
+ *              coefficients are multiplied by exp(-i chi(k)),
+ *              chi = pi lambda C1 |k|^2 + (pi/2) Cs lambda^3 |k|^4, so that a
+ *              positive C1 equals free propagation by C1 under Eq. 2. */
 typedef struct {
   double cell[3];
   int32_t n;
@@ -81,6 +87,8 @@ typedef struct {
   double alpha_mrad;
   double ring_width_mrad;
   int32_t n_rings;
+  double defocus_a;
+  double cs_a;
 } stem_params;
 
 /* Opaque plan: device-resident tables derived from stem_params (propagator
@@ -99,6 +107,13 @@ void stem_plan_destroy(stem_plan plan);
  * of aperture pixels |A| (host outputs; any may be NULL). */
 stem_status stem_plan_constants(stem_plan plan, double* lambda_a, double* sigma,
                                 int32_t* n_aperture);
+
+/* Replace the uniform rings by annular detectors with arbitrary edges (host
+ * array, mrad, strictly increasing, >= 0): detector i collects lambda |k| in
+ * [edges[i], edges[i+1]) inside the band limit; n_rings becomes n_edges - 1
+ * (<= 2048).  Covers 2D virtual detectors such as an ADF ring (two edges).
+ * Rebuilds the plan's tables with synchronous copies. */
+stem_status stem_plan_set_detector_edges(stem_plan plan, int32_t n_edges, const double* edges_mrad);
 
 /* Device status word of the plan: kernels whose waits are bounded (the
  * tensor-core beam sum) record STEM_ERR_TIMEOUT there instead of hanging.
@@ -126,7 +141,7 @@ stem_status stem_slice_potentials(stem_plan plan, const double* atoms_xyz, const
 /* ---------------------------------------------------------------------------
  * Multislice STEM (Eq. 1, Eq. 2; "Multislice Probe Simulations").
  * For each probe p at (x_p, y_p):
- *   psi_hat_p(k) = A(k) exp(-2 pi i k . r_p) / sqrt(|A|);  psi = IFFT(psi_hat)
+ *   psi_hat_p(k) = A(k) exp(-i chi(k)) exp(-2 pi i k . r_p) / sqrt(|A|);  psi = IFFT(psi_hat)
  *   for every slice n: psi <- IFFT( M P FFT(t_n psi) ),  P = exp(-i pi lambda dz |k|^2)
  *   (after the last slice the Fourier-space wave is kept)
  *   I_i(p) = sum_{k in ring i} |Psi_hat(k)|^2   (fraction of the incident intensity)
@@ -140,6 +155,14 @@ size_t stem_multislice_workspace(stem_plan plan, int32_t batch);
 stem_status stem_multislice_scan(stem_plan plan, const void* trans, const double* probe_xy,
                                  int64_t n_probes, int32_t batch, float weight, float* rings_out,
                                  void* workspace, size_t workspace_bytes, void* stream);
+
+/* 4D output of multislice ("Description of Algorithms": the whole probe
+ * diffraction pattern per probe position): dp_out float32 [n_probes][n][n] in
+ * FFT order, dp_out += weight * |Psi_hat|^2 inside the 2/3 band limit (other
+ * pixels are not written).  Otherwise as stem_multislice_scan. */
+stem_status stem_multislice_scan_4d(stem_plan plan, const void* trans, const double* probe_xy,
+                                    int64_t n_probes, int32_t batch, float weight, float* dp_out,
+                                    void* workspace, size_t workspace_bytes, void* stream);
 
 /* Multislice without a workspace argument, for callers that cannot allocate
  * device memory and have no scratch buffer to lend (for example a plugin whose
@@ -183,7 +206,7 @@ stem_status stem_prism_smatrix(stem_plan plan, const void* trans, int32_t f, ste
  * PRISM output ("Description of Algorithms", PRISM paragraph; "PRISM Probe
  * Simulations", last paragraph).  W = n / f.  For each probe:
  *   origin o_p = (floor(x_p/dx + 0.5), floor(y_p/dy + 0.5)) - W/2  (mod n)
- *   c_{p,b}   = exp(-2 pi i (m_b x_p / Lx + n_b y_p / Ly)) / sqrt(n_beams)
+ *   c_{p,b}   = exp(-i chi(k_b)) exp(-2 pi i (m_b x_p / Lx + n_b y_p / Ly)) / sqrt(n_beams)
  *               (phase reduced in FP64 on the device)
  *   Psi_p(u, v) = sum_b c_{p,b} S_b((o_p + (u, v)) mod n),  u, v in [0, W)
  *   I_i(p) = sum_{coarse k in ring i} |FFT_W(Psi_p)|^2 / W^4,
@@ -198,6 +221,14 @@ stem_status stem_prism_output(stem_plan plan, int32_t f, stem_storage storage, i
                               const void* smatrix, const double* probe_xy, int64_t n_probes,
                               int32_t chunk, float weight, float* rings_out,
                               void* workspace, size_t workspace_bytes, void* stream);
+
+/* 4D output of PRISM: dp_out float32 [n_probes][W][W] in FFT order on the
+ * window's coarse grid, dp_out += weight * |FFT_W(Psi_p)|^2 / W^4 inside the
+ * band limit (9 (mu^2 + nu^2) <= W^2).  Otherwise as stem_prism_output. */
+stem_status stem_prism_output_4d(stem_plan plan, int32_t f, stem_storage storage, int32_t engine,
+                                 const void* smatrix, const double* probe_xy, int64_t n_probes,
+                                 int32_t chunk, float weight, float* dp_out,
+                                 void* workspace, size_t workspace_bytes, void* stream);
 
 /* Stage of stem_prism_output exposed for stage-wise checks: the window waves
  * Psi_p (before the FFT) of n_probes probes (<= 65535), complex64

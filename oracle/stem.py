@@ -54,6 +54,8 @@ class Params:
     alpha_mrad: float
     ring_width_mrad: float
     n_rings: int
+    defocus: float = 0.0      # C1 in A
+    cs: float = 0.0           # spherical aberration C3 in A
 
     @property
     def lam(self) -> float:
@@ -76,7 +78,16 @@ def params_from(w) -> Params:
     """Params from a ``workloads.Workload``."""
     return Params(tuple(float(c) for c in w.cell), int(w.n), int(w.n_slices),
                   float(w.slice_dz), float(w.energy_kev), float(w.alpha_mrad),
-                  float(w.ring_width_mrad), int(w.n_rings))
+                  float(w.ring_width_mrad), int(w.n_rings), float(getattr(w, "defocus", 0.0)),
+                  float(getattr(w, "cs", 0.0)))
+
+
+def aberration_chi(p: Params, kx, ky):
+    """Aberration phase chi(k) = pi lambda C1 |k|^2 + (pi/2) Cs lambda^3 |k|^4 (rad).
+    The probe's Fourier coefficients carry exp(-i chi): with this sign a positive
+    defocus C1 equals free propagation by C1 under Eq. 2."""
+    k2 = kx * kx + ky * ky
+    return math.pi * p.lam * p.defocus * k2 + 0.5 * math.pi * p.cs * p.lam ** 3 * k2 * k2
 
 
 # ----------------------------------------------------------------------------
@@ -109,20 +120,27 @@ def aperture(p: Params) -> np.ndarray:
     return bandlimit_mask(p.n) & (angle_mrad(p) <= p.alpha_mrad)
 
 
-def ring_table(p: Params) -> np.ndarray:
-    """Ring index per FFT pixel (int64), -1 outside the band limit or beyond n_rings."""
-    r = np.floor(angle_mrad(p) / p.ring_width_mrad).astype(np.int64)
+def ring_table(p: Params, edges: Optional[Sequence[float]] = None) -> np.ndarray:
+    """Ring index per FFT pixel (int64), -1 outside the band limit or beyond the last
+    ring.  Uniform rings of ring_width_mrad, or annuli [edges[i], edges[i+1]) (mrad)."""
+    ang = angle_mrad(p)
+    if edges is None:
+        r = np.floor(ang / p.ring_width_mrad).astype(np.int64)
+        r[r >= p.n_rings] = -1
+    else:
+        e = np.asarray(edges, dtype=np.float64)
+        r = np.searchsorted(e, ang, side="right").astype(np.int64) - 1
+        r[r >= len(e) - 1] = -1
     r[~bandlimit_mask(p.n)] = -1
-    r[r >= p.n_rings] = -1
     return r
 
 
-def coarse_ring_table(p: Params, f: int) -> np.ndarray:
+def coarse_ring_table(p: Params, f: int, edges: Optional[Sequence[float]] = None) -> np.ndarray:
     """Ring table of a W x W window FFT, W = N/f: coarse frequency (nu, mu) is the
     fine frequency (f nu, f mu), so the table is the fine one sampled every f-th
     signed index."""
     w = p.n // f
-    fine = ring_table(p)
+    fine = ring_table(p, edges)
     mu = freq_index(w)
     idx = np.mod(f * mu, p.n)
     return fine[np.ix_(idx, idx)]
@@ -195,15 +213,16 @@ def transmission(p: Params, v: np.ndarray) -> np.ndarray:
 
 def probe_k(p: Params, xy: np.ndarray) -> np.ndarray:
     """Converged probes in Fourier space, [P, N, N]:
-    psi_hat_p(m, n) = A(m, n) exp(-2 pi i (m x_p / Lx + n y_p / Ly)) / sqrt(|A|)."""
+    psi_hat_p(m, n) = A(m, n) exp(-i chi(k)) exp(-2 pi i (m x_p / Lx + n y_p / Ly)) / sqrt(|A|)."""
     ap = aperture(p)
     norm = 1.0 / math.sqrt(int(ap.sum()))
     m = freq_index(p.n).astype(np.float64)
+    chi = aberration_chi(p, (m / p.cell[0])[None, :], (m / p.cell[1])[:, None])
     xy = np.atleast_2d(np.asarray(xy, dtype=np.float64))
     out = np.zeros((xy.shape[0], p.n, p.n), dtype=np.complex128)
     for i, (x, y) in enumerate(xy):
         ph = m[None, :] * x / p.cell[0] + m[:, None] * y / p.cell[1]
-        out[i] = np.where(ap, np.exp(-2j * math.pi * ph) * norm, 0.0)
+        out[i] = np.where(ap, np.exp(-2j * math.pi * ph - 1j * chi) * norm, 0.0)
     return out
 
 
@@ -236,15 +255,23 @@ def detector_rings(table: np.ndarray, n_rings: int, intensity: np.ndarray) -> np
     return out
 
 
-def multislice_rings(p: Params, trans: np.ndarray, xy: np.ndarray, chunk: int = 16) -> np.ndarray:
-    """Annular-ring output [P, n_rings] of multislice at probe positions xy [P, 2]."""
+def multislice_dp(p: Params, trans: np.ndarray, xy: np.ndarray) -> np.ndarray:
+    """4D output: |Psi_hat|^2 per probe, [P, N, N] in FFT order."""
+    return np.abs(multislice_k(p, trans, probe_real(p, xy))) ** 2
+
+
+def multislice_rings(p: Params, trans: np.ndarray, xy: np.ndarray, chunk: int = 16,
+                     edges: Optional[Sequence[float]] = None) -> np.ndarray:
+    """Annular-ring output [P, n_rings] of multislice at probe positions xy [P, 2]
+    (uniform rings, or the annuli between consecutive `edges` in mrad)."""
     xy = np.atleast_2d(np.asarray(xy, dtype=np.float64))
-    table = ring_table(p)
-    out = np.zeros((xy.shape[0], p.n_rings))
+    table = ring_table(p, edges)
+    n_out = p.n_rings if edges is None else len(edges) - 1
+    out = np.zeros((xy.shape[0], n_out))
     for c0 in range(0, xy.shape[0], chunk):
         psi = probe_real(p, xy[c0:c0 + chunk])
         psi_k = multislice_k(p, trans, psi)
-        out[c0:c0 + chunk] = detector_rings(table, p.n_rings, np.abs(psi_k) ** 2)
+        out[c0:c0 + chunk] = detector_rings(table, n_out, np.abs(psi_k) ** 2)
     return out
 
 
@@ -298,12 +325,13 @@ def prism_window_origin(p: Params, f: int, xy: np.ndarray) -> np.ndarray:
 
 
 def prism_coefficients(p: Params, beams: np.ndarray, xy: np.ndarray) -> np.ndarray:
-    """c[p, b] = exp(-2 pi i (m_b x_p / Lx + n_b y_p / Ly)) / sqrt(n_b)."""
+    """c[p, b] = exp(-i chi(k_b)) exp(-2 pi i (m_b x_p / Lx + n_b y_p / Ly)) / sqrt(n_b)."""
     xy = np.atleast_2d(np.asarray(xy, dtype=np.float64))
     mb = beams[:, 0].astype(np.float64)
     nb = beams[:, 1].astype(np.float64)
+    chi = aberration_chi(p, mb / p.cell[0], nb / p.cell[1])
     ph = xy[:, 0:1] * mb[None, :] / p.cell[0] + xy[:, 1:2] * nb[None, :] / p.cell[1]
-    return np.exp(-2j * math.pi * ph) / math.sqrt(beams.shape[0])
+    return np.exp(-2j * math.pi * ph - 1j * chi[None, :]) / math.sqrt(beams.shape[0])
 
 
 def prism_window_waves(p: Params, smatrix: np.ndarray, beams: np.ndarray, f: int,
@@ -320,6 +348,14 @@ def prism_window_waves(p: Params, smatrix: np.ndarray, beams: np.ndarray, f: int
         crop = smatrix[:, rows][:, :, cols]                  # [n_b, W, W]
         out[i] = np.tensordot(coef[i], crop, axes=(0, 0))
     return out
+
+
+def prism_dp(p: Params, smatrix: np.ndarray, beams: np.ndarray, f: int, xy: np.ndarray) -> np.ndarray:
+    """PRISM 4D output on the window grid: |FFT_W(Psi_p)|^2 / W^4 inside the band
+    limit (coarse (mu, nu) standing for (f mu, f nu)), [P, W, W] in FFT order."""
+    w = p.n // f
+    spec = np.fft.fft2(prism_window_waves(p, smatrix, beams, f, xy), axes=(-2, -1))
+    return np.abs(spec) ** 2 / float(w) ** 4 * bandlimit_mask(w)[None]
 
 
 def prism_rings(p: Params, smatrix: np.ndarray, beams: np.ndarray, f: int,

@@ -27,7 +27,7 @@ ENGINE = {"auto": 0, "simt": 1, "tensor": 2}
 class StemParams(ctypes.Structure):
     _fields_ = [("cell", c_double * 3), ("n", c_int32), ("n_slices", c_int32), ("slice_dz", c_double),
                 ("energy_kev", c_double), ("alpha_mrad", c_double), ("ring_width_mrad", c_double),
-                ("n_rings", c_int32)]
+                ("n_rings", c_int32), ("defocus_a", c_double), ("cs_a", c_double)]
 
 
 class StemError(RuntimeError):
@@ -52,6 +52,11 @@ SIGNATURES = {
                                        c_void_p, c_size_t, c_void_p]),
     "stem_multislice_scan_noalloc": (c_int32, [c_void_p, c_void_p, c_void_p, c_int64, c_int32, c_float,
                                                c_void_p, c_void_p]),
+    "stem_multislice_scan_4d": (c_int32, [c_void_p, c_void_p, c_void_p, c_int64, c_int32, c_float, c_void_p,
+                                          c_void_p, c_size_t, c_void_p]),
+    "stem_prism_output_4d": (c_int32, [c_void_p, c_int32, c_int32, c_int32, c_void_p, c_void_p, c_int64, c_int32,
+                                       c_float, c_void_p, c_void_p, c_size_t, c_void_p]),
+    "stem_plan_set_detector_edges": (c_int32, [c_void_p, c_int32, c_void_p]),
     "stem_prism_beams": (c_int32, [c_void_p, c_int32, POINTER(c_int32), c_void_p]),
     "stem_prism_smatrix_bytes": (c_size_t, [c_void_p, c_int32, c_int32]),
     "stem_prism_smatrix_workspace": (c_size_t, [c_void_p, c_int32]),

@@ -72,13 +72,13 @@ class Plan:
     """A stem_plan: grid, optics and detector tables on the current CUDA device."""
 
     def __init__(self, cell, n, n_slices, slice_dz, energy_kev, alpha_mrad, ring_width_mrad, n_rings,
-                 device=None):
+                 device=None, defocus=0.0, cs=0.0):
         lib = _lib.load()
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else
                                    torch.device(device).index or 0)
         self.params = StemParams((ctypes.c_double * 3)(*[float(c) for c in cell]), int(n), int(n_slices),
                                  float(slice_dz), float(energy_kev), float(alpha_mrad),
-                                 float(ring_width_mrad), int(n_rings))
+                                 float(ring_width_mrad), int(n_rings), float(defocus), float(cs))
         handle = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             check(lib.stem_plan_create(ctypes.byref(self.params), ctypes.byref(handle)), "stem_plan_create")
@@ -94,7 +94,7 @@ class Plan:
     @classmethod
     def from_workload(cls, w, device=None) -> "Plan":
         return cls(w.cell, w.n, w.n_slices, w.slice_dz, w.energy_kev, w.alpha_mrad, w.ring_width_mrad,
-                   w.n_rings, device=device)
+                   w.n_rings, device=device, defocus=getattr(w, "defocus", 0.0), cs=getattr(w, "cs", 0.0))
 
     def close(self):
         if getattr(self, "_h", None) and self._h.value:
@@ -151,6 +151,32 @@ class Plan:
               "stem_multislice_scan")
         return rings
 
+    def multislice_4d(self, trans: torch.Tensor, probe_xy: torch.Tensor, batch: int = 64,
+                      dp: Optional[torch.Tensor] = None, weight: float = 1.0,
+                      workspace: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """Whole diffraction pattern per probe, float32 [P, N, N] in FFT order."""
+        lib = _lib.load()
+        trans = _need(trans, torch.complex64, "trans", (self.n_slices, self.n, self.n))
+        probe_xy = _need(probe_xy, torch.float64, "probe_xy")
+        npr = probe_xy.shape[0]
+        if dp is None:
+            dp = torch.zeros((npr, self.n, self.n), dtype=torch.float32, device=self.device)
+        else:
+            dp = _need(dp, torch.float32, "dp", (npr, self.n, self.n))
+        batch = int(max(1, min(batch, max(npr, 1))))
+        ws = workspace if workspace is not None else self.multislice_workspace(batch)
+        check(lib.stem_multislice_scan_4d(self._h, _ptr(trans), _ptr(probe_xy), npr, batch, float(weight), _ptr(dp),
+                                          _ptr(ws), ws.numel(), _stream(self.device)), "stem_multislice_scan_4d")
+        return dp
+
+    def set_detector_edges(self, edges_mrad) -> None:
+        """Annular detectors [edges[i], edges[i+1]) in mrad instead of uniform rings."""
+        lib = _lib.load()
+        e = np.ascontiguousarray(np.asarray(edges_mrad, dtype=np.float64))
+        check(lib.stem_plan_set_detector_edges(self._h, len(e), e.ctypes.data_as(ctypes.c_void_p)),
+              "stem_plan_set_detector_edges")
+        self.n_rings = len(e) - 1
+
     # ------------------------------------------------------------------ PRISM
     def prism_beams(self, f: int) -> np.ndarray:
         lib = _lib.load()
@@ -199,6 +225,22 @@ class Plan:
                                     _stream(self.device)), "stem_prism_output")
         return rings
 
+    def prism_output_4d(self, smat: SMatrix, probe_xy: torch.Tensor, chunk: int = 1024, engine: str = "auto",
+                        dp: Optional[torch.Tensor] = None, weight: float = 1.0) -> torch.Tensor:
+        """PRISM diffraction patterns on the window grid, float32 [P, W, W] (FFT order, / W^4)."""
+        lib = _lib.load()
+        probe_xy = _need(probe_xy, torch.float64, "probe_xy")
+        npr = probe_xy.shape[0]
+        w = self.n // smat.f
+        if dp is None:
+            dp = torch.zeros((npr, w, w), dtype=torch.float32, device=self.device)
+        chunk = int(max(1, min(chunk, max(npr, 1), 65535)))
+        ws = self.prism_output_workspace(smat.f, chunk)
+        check(lib.stem_prism_output_4d(self._h, smat.f, STORAGE[smat.storage], ENGINE[engine], _ptr(smat.buf),
+                                       _ptr(probe_xy), npr, chunk, float(weight), _ptr(dp), _ptr(ws), ws.numel(),
+                                       _stream(self.device)), "stem_prism_output_4d")
+        return dp
+
     def prism_windows(self, smat: SMatrix, probe_xy: torch.Tensor, engine: str = "auto") -> torch.Tensor:
         lib = _lib.load()
         probe_xy = _need(probe_xy, torch.float64, "probe_xy")
@@ -242,6 +284,6 @@ def footprint_bytes(w, algo: str = "ms", f: int = 1, storage: str = "f32", batch
     lib = _lib.load()
     p = StemParams((ctypes.c_double * 3)(*[float(c) for c in w.cell]), int(w.n), int(w.n_slices),
                    float(w.slice_dz), float(w.energy_kev), float(w.alpha_mrad), float(w.ring_width_mrad),
-                   int(w.n_rings))
+                   int(w.n_rings), float(getattr(w, "defocus", 0.0)), float(getattr(w, "cs", 0.0)))
     return int(lib.stem_footprint_bytes(ctypes.byref(p), 0 if algo == "ms" else 1, f, STORAGE[storage],
                                         w.n_probes, batch))

@@ -5,6 +5,7 @@
 // PRISM beam lists) and sequences the kernels on the caller's stream.  No
 // simulation arithmetic runs on the host.
 #include <algorithm>
+#include <vector>
 #include <atomic>
 #include <cmath>
 #include <cstring>
@@ -51,7 +52,7 @@ stem_status check_params(const stem_params* p) {
   if (!is_pow2(p->n) || p->n < 8 || p->n > 2048) return STEM_ERR_UNSUPPORTED;
   if (!(p->cell[0] > 0.0) || !(p->cell[1] > 0.0) || p->n_slices < 1 || !(p->slice_dz > 0.0) ||
       !(p->energy_kev > 0.0) || !(p->alpha_mrad >= 0.0) || !(p->ring_width_mrad > 0.0) || p->n_rings < 1 ||
-      p->n_rings > kMaxRings)
+      p->n_rings > kMaxRings || !std::isfinite(p->defocus_a) || !std::isfinite(p->cs_a))
     return STEM_ERR_INVALID;
   return STEM_OK;
 }
@@ -73,6 +74,62 @@ int count_beams(const stem_params* p, int f, double lam) {
     }
   }
   return nb;
+}
+
+
+// Ring of scattering angle `ang` (mrad): uniform rings of ring_width_mrad, or
+// [edges[i], edges[i+1]) when detector edges are set; -1 outside every ring.
+int ring_of(double ang, const stem_params& p, const std::vector<double>& edges) {
+  if (edges.empty()) {
+    const double r = std::floor(ang / p.ring_width_mrad);
+    return r < (double)p.n_rings ? (int)r : -1;
+  }
+  const int i = (int)(std::upper_bound(edges.begin(), edges.end(), ang) - edges.begin()) - 1;
+  return (i >= 0 && i < (int)edges.size() - 1) ? i : -1;
+}
+
+// Fine look-up table (aperture bit, ring index) decided in FP64; returns |A|.
+int build_fine_lut(const stem_params& p, double lam, const std::vector<double>& edges, std::vector<uint16_t>& lut) {
+  const int n = p.n;
+  const double lx = p.cell[0], ly = p.cell[1];
+  lut.assign((size_t)n * n, kLutNoRing);
+  int n_ap = 0;
+  for (int i = 0; i < n; ++i) {
+    const int nn = freq(i, n);
+    const double ky = (double)nn / ly;
+    for (int j = 0; j < n; ++j) {
+      const int mm = freq(j, n);
+      const double kx = (double)mm / lx;
+      const bool mask = 9LL * ((long long)mm * mm + (long long)nn * nn) <= (long long)n * n;
+      const double k = std::sqrt(kx * kx + ky * ky);
+      const double ang = (lam * k) * 1000.0;
+      uint16_t v = kLutNoRing;
+      if (mask) {
+        const int r = ring_of(ang, p, edges);
+        if (r >= 0) v = (uint16_t)r;
+        if (ang <= p.alpha_mrad) {
+          v |= kLutAperture;
+          ++n_ap;
+        }
+      }
+      lut[(size_t)i * n + j] = v;
+    }
+  }
+  return n_ap;
+}
+
+// Window table for f: window frequency (mu, nu) is the fine frequency (f mu, f nu).
+std::vector<uint16_t> coarse_lut(const std::vector<uint16_t>& lut, int n, int f) {
+  const int w = n / f;
+  std::vector<uint16_t> coarse((size_t)w * w);
+  for (int v = 0; v < w; ++v) {
+    const int fi = ((f * freq(v, w)) % n + n) % n;
+    for (int u = 0; u < w; ++u) {
+      const int fj = ((f * freq(u, w)) % n + n) % n;
+      coarse[(size_t)v * w + u] = lut[(size_t)fi * n + fj];
+    }
+  }
+  return coarse;
 }
 
 }  // namespace
@@ -101,6 +158,7 @@ void stem_plan_destroy(stem_plan pl) {
   for (int i = 0; i <= kMaxLog2F; ++i) {
     cudaFree(pl->lut[i]);
     cudaFree(pl->beams[i]);
+    cudaFree(pl->beam_turns[i]);
   }
   delete pl;
 }
@@ -121,30 +179,8 @@ stem_status stem_plan_create(const stem_params* params, stem_plan* out) {
   const double lx = params->cell[0], ly = params->cell[1];
 
   // Fine look-up table: aperture bit and ring index, decided in FP64.
-  std::vector<uint16_t> lut((size_t)n * n);
-  int n_ap = 0;
-  for (int i = 0; i < n; ++i) {
-    const int nn = freq(i, n);
-    const double ky = (double)nn / ly;
-    for (int j = 0; j < n; ++j) {
-      const int mm = freq(j, n);
-      const double kx = (double)mm / lx;
-      const bool mask = 9LL * ((long long)mm * mm + (long long)nn * nn) <= (long long)n * n;
-      const double k = std::sqrt(kx * kx + ky * ky);
-      const double ang = (pl->lam * k) * 1000.0;
-      uint16_t v = kLutNoRing;
-      if (mask) {
-        const double r = std::floor(ang / params->ring_width_mrad);
-        if (r < (double)params->n_rings) v = (uint16_t)r;
-        if (ang <= params->alpha_mrad) {
-          v |= kLutAperture;
-          ++n_ap;
-        }
-      }
-      lut[(size_t)i * n + j] = v;
-    }
-  }
-  pl->n_aperture = n_ap;
+  std::vector<uint16_t> lut;
+  pl->n_aperture = build_fine_lut(*params, pl->lam, pl->edges, lut);
 
   // Propagator factors exp(-i pi lambda dz (m/L)^2) per axis (Eq. 2 is separable).
   std::vector<float2> px(n), py(n);
@@ -171,15 +207,7 @@ stem_status stem_plan_create(const stem_params* params, stem_plan* out) {
     const int f = 1 << lf;
     if (f > n / 8) break;
     const int w = n / f;
-    // coarse table: window frequency (mu, nu) is the fine frequency (f mu, f nu)
-    std::vector<uint16_t> coarse((size_t)w * w);
-    for (int v = 0; v < w; ++v) {
-      const int fi = ((f * freq(v, w)) % n + n) % n;
-      for (int u = 0; u < w; ++u) {
-        const int fj = ((f * freq(u, w)) % n + n) % n;
-        coarse[(size_t)v * w + u] = lut[(size_t)fi * n + fj];
-      }
-    }
+    const std::vector<uint16_t> coarse = coarse_lut(lut, n, f);
     upload(reinterpret_cast<void**>(&pl->lut[lf]), coarse.data(), coarse.size() * sizeof(uint16_t));
     // PRISM beams: aperture pixels on every f-th frequency, ordered by n then m.
     std::vector<int2>& bl = pl->h_beams[lf];
@@ -193,6 +221,16 @@ stem_status stem_plan_create(const stem_params* params, stem_plan* out) {
     }
     pl->n_beams[lf] = (int)bl.size();
     upload(reinterpret_cast<void**>(&pl->beams[lf]), bl.data(), bl.size() * sizeof(int2));
+    // aberration phase of each beam in turns, chi(k_b) / (2 pi) reduced mod 1 in FP64
+    std::vector<double> turns(bl.size());
+    for (size_t b = 0; b < bl.size(); ++b) {
+      const double kx = (double)bl[b].x / lx, ky = (double)bl[b].y / ly;
+      const double k2 = kx * kx + ky * ky;
+      const double t = 0.5 * pl->lam * params->defocus_a * k2 +
+                       0.25 * params->cs_a * pl->lam * pl->lam * pl->lam * k2 * k2;
+      turns[b] = t - std::floor(t);
+    }
+    upload(reinterpret_cast<void**>(&pl->beam_turns[lf]), turns.data(), turns.size() * sizeof(double));
   }
   if (e != cudaSuccess) {
     stem_plan_destroy(pl);
@@ -220,6 +258,30 @@ stem_status stem_plan_constants(stem_plan pl, double* lambda_a, double* sigma, i
   return STEM_OK;
 }
 
+stem_status stem_plan_set_detector_edges(stem_plan pl, int32_t n_edges, const double* edges_mrad) {
+  if (!pl || n_edges < 2 || n_edges - 1 > kMaxRings || !edges_mrad) return STEM_ERR_INVALID;
+  for (int i = 0; i < n_edges; ++i) {
+    if (!std::isfinite(edges_mrad[i]) || edges_mrad[i] < 0.0) return STEM_ERR_INVALID;
+    if (i > 0 && !(edges_mrad[i] > edges_mrad[i - 1])) return STEM_ERR_INVALID;
+  }
+  std::vector<double> edges(edges_mrad, edges_mrad + n_edges);
+  stem_params p = pl->p;
+  p.n_rings = n_edges - 1;
+  std::vector<uint16_t> lut;
+  build_fine_lut(p, pl->lam, edges, lut);
+  for (int lf = 0; lf <= kMaxLog2F; ++lf) {
+    const int f = 1 << lf;
+    if (f > pl->n / 8 || !pl->lut[lf]) break;
+    const std::vector<uint16_t> coarse = coarse_lut(lut, pl->n, f);
+    if (cudaMemcpy(pl->lut[lf], coarse.data(), coarse.size() * sizeof(uint16_t), cudaMemcpyHostToDevice) !=
+        cudaSuccess)
+      return STEM_ERR_CUDA;
+  }
+  pl->edges = edges;
+  pl->p.n_rings = p.n_rings;
+  return STEM_OK;
+}
+
 // ----------------------------------------------------------------------------- potentials
 size_t stem_slice_potentials_workspace(stem_plan pl, int64_t n_atoms) {
   if (!pl || n_atoms < 0 || pl->n < 64) return 0;
@@ -242,11 +304,14 @@ size_t stem_multislice_workspace(stem_plan pl, int32_t batch) {
   return (size_t)batch * pl->n * pl->n * sizeof(float2);
 }
 
-stem_status stem_multislice_scan(stem_plan pl, const void* trans, const double* probe_xy, int64_t n_probes,
-                                 int32_t batch, float weight, float* rings_out, void* ws, size_t ws_bytes,
-                                 void* stream) {
-  if (!pl || !trans || n_probes < 0 || (n_probes > 0 && (!probe_xy || !rings_out)) || batch < 1 || batch > 65535 ||
-      !ws)
+// The slice loop of Eq. 1 and Eq. 2 over batches of probes; the last column
+// pass bins |Psi_hat|^2 into rings (dp == NULL) or accumulates the whole
+// diffraction pattern into dp.
+static stem_status run_multislice(stem_plan pl, const void* trans, const double* probe_xy, int64_t n_probes,
+                                  int32_t batch, float weight, float* rings_out, float* dp_out, void* ws,
+                                  size_t ws_bytes, void* stream) {
+  if (!pl || !trans || n_probes < 0 || (n_probes > 0 && (!probe_xy || (!rings_out && !dp_out))) || batch < 1 ||
+      batch > 65535 || !ws)
     return STEM_ERR_INVALID;
   const int n = pl->n;
   if (n < 64) return STEM_ERR_UNSUPPORTED;
@@ -265,20 +330,38 @@ stem_status stem_multislice_scan(stem_plan pl, const void* trans, const double* 
   a.inv_ly = 1.0 / pl->p.cell[1];
   a.probe_norm = (float)(1.0 / (std::sqrt((double)std::max(pl->n_aperture, 1)) * (double)plane));
   a.band = 1;   // the last column pass reads waves whose out-of-band columns were never written
+  a.chi_c1 = 0.5 * pl->lam * pl->p.defocus_a;
+  a.chi_c3 = 0.25 * pl->p.cs_a * pl->lam * pl->lam * pl->lam;
   const float2* t = static_cast<const float2*>(trans);
+  const int last = dp_out ? COL_DP : COL_DET;
   for (int64_t p0 = 0; p0 < n_probes; p0 += batch) {
     a.batch = (int)std::min<int64_t>(batch, n_probes - p0);
     a.probe_xy = probe_xy + 2 * p0;
-    a.rings = rings_out + p0 * pl->p.n_rings;
+    if (rings_out) a.rings = rings_out + p0 * pl->p.n_rings;
+    if (dp_out) a.dp = dp_out + p0 * plane;
     cudaError_t e = launch_col_pass(n, COL_PROBE_INIT, a, s);
     for (int sl = 0; sl < pl->p.n_slices && e == cudaSuccess; ++sl) {
       a.trans = t + sl * plane;
       e = launch_row_pass(n, ROW_SLICE, a, s);
-      if (e == cudaSuccess) e = launch_col_pass(n, sl + 1 < pl->p.n_slices ? COL_SLICE : COL_DET, a, s);
+      if (e == cudaSuccess) e = launch_col_pass(n, sl + 1 < pl->p.n_slices ? COL_SLICE : last, a, s);
     }
     if (e != cudaSuccess) return STEM_ERR_CUDA;
   }
   return STEM_OK;
+}
+
+stem_status stem_multislice_scan(stem_plan pl, const void* trans, const double* probe_xy, int64_t n_probes,
+                                 int32_t batch, float weight, float* rings_out, void* ws, size_t ws_bytes,
+                                 void* stream) {
+  if (n_probes > 0 && !rings_out) return STEM_ERR_INVALID;
+  return run_multislice(pl, trans, probe_xy, n_probes, batch, weight, rings_out, nullptr, ws, ws_bytes, stream);
+}
+
+stem_status stem_multislice_scan_4d(stem_plan pl, const void* trans, const double* probe_xy, int64_t n_probes,
+                                    int32_t batch, float weight, float* dp_out, void* ws, size_t ws_bytes,
+                                    void* stream) {
+  if (n_probes > 0 && !dp_out) return STEM_ERR_INVALID;
+  return run_multislice(pl, trans, probe_xy, n_probes, batch, weight, nullptr, dp_out, ws, ws_bytes, stream);
 }
 
 // ----------------------------------------------------------------------------- PRISM S-matrix
@@ -367,6 +450,7 @@ static stem_status output_common(stem_plan pl, int32_t f, stem_storage storage, 
   o.n_beams = L.n_beams;
   o.nbp = L.nbp;
   o.beams = pl->beams[lf];
+  o.beam_turns = pl->beam_turns[lf];
   o.smatrix = smatrix;
   o.scales = static_cast<const float*>(smatrix);
   o.sdata = static_cast<const char*>(smatrix) + L.data_offset;
@@ -393,13 +477,13 @@ stem_status stem_prism_windows(stem_plan pl, int32_t f, stem_storage storage, in
                                          static_cast<char*>(ws), L, as_stream(stream)));
 }
 
-stem_status stem_prism_output(stem_plan pl, int32_t f, stem_storage storage, int32_t engine, const void* smatrix,
-                              const double* probe_xy, int64_t n_probes, int32_t chunk, float weight,
-                              float* rings_out, void* ws, size_t ws_bytes, void* stream) {
+static stem_status run_prism_output(stem_plan pl, int32_t f, stem_storage storage, int32_t engine, const void* smatrix,
+                                    const double* probe_xy, int64_t n_probes, int32_t chunk, float weight,
+                                    float* rings_out, float* dp_out, void* ws, size_t ws_bytes, void* stream) {
   OutputArgs o;
   stem_status st = output_common(pl, f, storage, engine, smatrix, o);
   if (st != STEM_OK) return st;
-  if (n_probes < 0 || (n_probes > 0 && (!probe_xy || !rings_out)) || chunk < 1 || chunk > 65535 || !ws)
+  if (n_probes < 0 || (n_probes > 0 && (!probe_xy || (!rings_out && !dp_out))) || chunk < 1 || chunk > 65535 || !ws)
     return STEM_ERR_INVALID;
   const OutputWs L = output_workspace_layout(o.n, f, chunk, o.nbp);
   if (ws_bytes < L.total) return STEM_ERR_NOMEM;
@@ -416,13 +500,30 @@ stem_status stem_prism_output(stem_plan pl, int32_t f, stem_storage storage, int
     a.batch = np;
     a.lut = pl->lut[lf];
     a.n_rings = pl->p.n_rings;
-    a.rings = rings_out + c0 * pl->p.n_rings;
+    if (rings_out) a.rings = rings_out + c0 * pl->p.n_rings;
+    if (dp_out) a.dp = dp_out + c0 * (size_t)o.w * o.w;
     a.ring_scale = (float)(weight / w4);
     if (e == cudaSuccess) e = launch_row_pass(o.w, ROW_FFT, a, s);
-    if (e == cudaSuccess) e = launch_col_pass(o.w, COL_DET, a, s);
+    if (e == cudaSuccess) e = launch_col_pass(o.w, dp_out ? COL_DP : COL_DET, a, s);
     if (e != cudaSuccess) return STEM_ERR_CUDA;
   }
   return STEM_OK;
+}
+
+stem_status stem_prism_output(stem_plan pl, int32_t f, stem_storage storage, int32_t engine, const void* smatrix,
+                              const double* probe_xy, int64_t n_probes, int32_t chunk, float weight,
+                              float* rings_out, void* ws, size_t ws_bytes, void* stream) {
+  if (n_probes > 0 && !rings_out) return STEM_ERR_INVALID;
+  return run_prism_output(pl, f, storage, engine, smatrix, probe_xy, n_probes, chunk, weight, rings_out, nullptr, ws,
+                          ws_bytes, stream);
+}
+
+stem_status stem_prism_output_4d(stem_plan pl, int32_t f, stem_storage storage, int32_t engine, const void* smatrix,
+                                 const double* probe_xy, int64_t n_probes, int32_t chunk, float weight,
+                                 float* dp_out, void* ws, size_t ws_bytes, void* stream) {
+  if (n_probes > 0 && !dp_out) return STEM_ERR_INVALID;
+  return run_prism_output(pl, f, storage, engine, smatrix, probe_xy, n_probes, chunk, weight, nullptr, dp_out, ws,
+                          ws_bytes, stream);
 }
 
 // ----------------------------------------------------------------------------- detector, FFT

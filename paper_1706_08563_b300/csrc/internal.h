@@ -34,10 +34,12 @@ struct PassArgs {
   const int2* beams = nullptr;       // [batch] (m, n) (offset)
   unsigned* beam_max = nullptr;      // [batch] float bits of max(|Re|, |Im|)
   int band = 0;                      // COL_DET ends a slice loop: only in-band columns hold data
+  double chi_c1 = 0.0, chi_c3 = 0.0; // aberration phase in turns: chi_c1 |k|^2 + chi_c3 |k|^4
+  float* dp = nullptr;               // COL_DP: [batch][N][N] intensities, += ring_scale |psi|^2
 };
 
 enum RowMode { ROW_SLICE = 0, ROW_BEAM0 = 1, ROW_IFFT_MAX = 2, ROW_FFT = 3, ROW_IFFT = 4 };
-enum ColMode { COL_SLICE = 0, COL_DET = 1, COL_PROBE_INIT = 2, COL_FFT = 3, COL_IFFT = 4 };
+enum ColMode { COL_SLICE = 0, COL_DET = 1, COL_PROBE_INIT = 2, COL_FFT = 3, COL_IFFT = 4, COL_DP = 5 };
 
 // Counts this library's kernel launches (stem_launch_count); called at every launch site.
 void note_launch();
@@ -73,6 +75,7 @@ struct OutputArgs {
   int n = 0, f = 0, w = 0, storage = 0, engine = 0;
   int n_beams = 0, nbp = 0;
   const int2* beams = nullptr;
+  const double* beam_turns = nullptr;   // chi(k_b) / (2 pi) per beam, reduced mod 1
   const void* smatrix = nullptr;
   const float* scales = nullptr;
   const void* sdata = nullptr;
@@ -108,6 +111,8 @@ struct stem_plan_s {
   uint16_t* lut[stem::kMaxLog2F + 1] = {};
   int2* beams[stem::kMaxLog2F + 1] = {};
   int n_beams[stem::kMaxLog2F + 1] = {};
+  double* beam_turns[stem::kMaxLog2F + 1] = {};   // chi(k_b) / (2 pi) mod 1 per beam
   std::vector<int2> h_beams[stem::kMaxLog2F + 1];
   int* status = nullptr;   // device status word, 0 = ok
+  std::vector<double> edges;   // detector edges (mrad) when set, else uniform rings
 };

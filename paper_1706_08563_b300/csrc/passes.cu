@@ -277,6 +277,18 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, ColCfg<N>::MINB) k_col_pas
         const float acc = ring_acc[i];
         if (acc != 0.0f) atomicAdd(out + i, acc * a.ring_scale);
       }
+    } else if constexpr (MODE == COL_DP) {
+      // 4D output: the whole diffraction pattern of the wave inside the 2/3
+      // band limit (pixels outside it, including stale out-of-band columns of a
+      // band tile, are left untouched)
+      float* out = a.dp + (size_t)wave * N * N + col;
+      const int m = signed_freq(col, N);
+#pragma unroll
+      for (int q = 0; q < E; ++q) {
+        const int ky = t + q * T;
+        const int n = signed_freq(ky, N);
+        if (9 * (m * m + n * n) <= N * N) out[(size_t)ky * N] += cabs2(v[q]) * a.ring_scale;
+      }
     } else {
 #pragma unroll
       for (int q = 0; q < E; ++q) w[(size_t)(t + q * T) * N] = v[q];
@@ -363,6 +375,7 @@ template <int N>
 static cudaError_t col_dispatch(int mode, const PassArgs& a, cudaStream_t s) {
   switch (mode) {
     case COL_DET: return a.band ? col_launch<N, COL_DET, true>(a, s) : col_launch<N, COL_DET, false>(a, s);
+    case COL_DP: return a.band ? col_launch<N, COL_DP, true>(a, s) : col_launch<N, COL_DP, false>(a, s);
     case COL_FFT: return col_launch<N, COL_FFT, false>(a, s);
     case COL_IFFT: return col_launch<N, COL_IFFT, false>(a, s);
     default: break;

@@ -160,9 +160,10 @@ OutputWs output_workspace_layout(int n, int f, int chunk, int nbp) {
   return L;
 }
 
-// c[p][re|im][b] = exp(-2 pi i (m_b x_p / Lx + n_b y_p / Ly)) * norm * s_b; the
-// phase is reduced modulo 1 in FP64 before the FP32 sine/cosine.
-__global__ void k_coefficients(const double* __restrict__ xy, const int2* __restrict__ beams, int n_beams, int nbp,
+// c[p][re|im][b] = exp(-i chi(k_b)) exp(-2 pi i (m_b x_p / Lx + n_b y_p / Ly)) * norm * s_b;
+// the phase (in turns) is reduced modulo 1 in FP64 before the FP32 sine/cosine.
+__global__ void k_coefficients(const double* __restrict__ xy, const int2* __restrict__ beams,
+                               const double* __restrict__ turns, int n_beams, int nbp,
                                const float* __restrict__ scales, double inv_lx, double inv_ly, float norm,
                                float* __restrict__ coef) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
@@ -171,7 +172,7 @@ __global__ void k_coefficients(const double* __restrict__ xy, const int2* __rest
   float re = 0.0f, im = 0.0f;
   if (b < n_beams) {
     const int2 mn = beams[b];
-    double th = (double)mn.x * xy[2 * p] * inv_lx + (double)mn.y * xy[2 * p + 1] * inv_ly;
+    double th = (double)mn.x * xy[2 * p] * inv_lx + (double)mn.y * xy[2 * p + 1] * inv_ly + turns[b];
     th -= rint(th);
     float s, c;
     sincospif(-2.0f * (float)th, &s, &c);
@@ -369,8 +370,8 @@ cudaError_t prism_windows_chunk(const OutputArgs& o, const double* probe_xy, int
 
   dim3 cg((o.nbp + 127) / 128, np);
   if (!tensor) {
-    note_launch(), k_coefficients<<<cg, 128, 0, s>>>(probe_xy, o.beams, o.n_beams, o.nbp, o.scales, 1.0 / o.lx,
-                                                    1.0 / o.ly, o.coef_norm, coef);
+    note_launch(), k_coefficients<<<cg, 128, 0, s>>>(probe_xy, o.beams, o.beam_turns, o.n_beams, o.nbp, o.scales,
+                                                    1.0 / o.lx, 1.0 / o.ly, o.coef_norm, coef);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   if ((e = cudaMemsetAsync(counts, 0, n_tiles * sizeof(int), s)) != cudaSuccess) return e;

@@ -139,16 +139,17 @@ __device__ __forceinline__ int find_item_tile(const int* __restrict__ work, int 
 
 // Coefficients as the B operand: row (p, h) of length K = 2 nbp, 16-bit.
 template <typename T>
-__global__ void k_coefficients_umma(const double* __restrict__ xy, const int2* __restrict__ beams, int n_beams,
-                                    int nbp, const float* __restrict__ scales, double inv_lx, double inv_ly,
-                                    float norm, T* __restrict__ coef) {
+__global__ void k_coefficients_umma(const double* __restrict__ xy, const int2* __restrict__ beams,
+                                    const double* __restrict__ turns, int n_beams, int nbp,
+                                    const float* __restrict__ scales, double inv_lx, double inv_ly, float norm,
+                                    T* __restrict__ coef) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   const int p = blockIdx.y;
   if (b >= nbp) return;
   float re = 0.0f, im = 0.0f;
   if (b < n_beams) {
     const int2 mn = beams[b];
-    double th = (double)mn.x * xy[2 * p] * inv_lx + (double)mn.y * xy[2 * p + 1] * inv_ly;
+    double th = (double)mn.x * xy[2 * p] * inv_lx + (double)mn.y * xy[2 * p + 1] * inv_ly + turns[b];
     th -= rint(th);
     float s, c;
     sincospif(-2.0f * (float)th, &s, &c);
@@ -322,7 +323,7 @@ cudaError_t launch_beam_sum_umma(const OutputArgs& o, int np, const double* prob
   const size_t smem = umma_smem_bytes();
   cudaError_t e;
   if (o.storage == STEM_F16) {
-    note_launch(), k_coefficients_umma<__half><<<cg, 128, 0, s>>>(probe_xy, o.beams, o.n_beams, o.nbp, o.scales,
+    note_launch(), k_coefficients_umma<__half><<<cg, 128, 0, s>>>(probe_xy, o.beams, o.beam_turns, o.n_beams, o.nbp, o.scales,
                                                                  inv_lx, inv_ly, o.coef_norm, static_cast<__half*>(coef));
     if ((e = cudaFuncSetAttribute(k_beam_sum_umma<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
         cudaSuccess)
@@ -332,7 +333,8 @@ cudaError_t launch_beam_sum_umma(const OutputArgs& o, int np, const double* prob
         work, list, n_tiles, windows, o.status);
   } else if (o.storage == STEM_BF16) {
     note_launch(), k_coefficients_umma<__nv_bfloat16><<<cg, 128, 0, s>>>(
-        probe_xy, o.beams, o.n_beams, o.nbp, o.scales, inv_lx, inv_ly, o.coef_norm, static_cast<__nv_bfloat16*>(coef));
+        probe_xy, o.beams, o.beam_turns, o.n_beams, o.nbp, o.scales, inv_lx, inv_ly, o.coef_norm,
+        static_cast<__nv_bfloat16*>(coef));
     if ((e = cudaFuncSetAttribute(k_beam_sum_umma<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem)) != cudaSuccess)
       return e;

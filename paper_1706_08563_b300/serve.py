@@ -199,7 +199,7 @@ class Server:
     def lane_key(req: SimRequest) -> tuple:
         w = req.workload
         return (req.specimen, tuple(w.cell), w.n, w.n_slices, w.slice_dz, w.energy_kev, w.alpha_mrad,
-                w.ring_width_mrad, w.n_rings, req.algo, req.f if req.algo == "prism" else 1,
+                w.ring_width_mrad, w.n_rings, getattr(w, "defocus", 0.0), getattr(w, "cs", 0.0), req.algo, req.f if req.algo == "prism" else 1,
                 req.storage if req.algo == "prism" else "f32")
 
     def footprint(self, req: SimRequest, capacity: int) -> int:

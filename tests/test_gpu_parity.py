@@ -338,3 +338,77 @@ def test_prism_smatrix_tiled_sizes(api, n, f, storage):
     out = plan.prism_output(sm, dev(xy)).cpu().numpy()
     check_rings(out, O.prism_rings(p, O.prism_smatrix(p, tref, beams), beams, f, xy),
                 FP32_TOL if storage == "f32" else LOWP_TOL)
+
+
+# -------------------------------------------------------------- aberrations
+@pytest.mark.parametrize("defocus,cs", [(80.0, 0.0), (-40.0, 5e5)])
+def test_multislice_and_prism_with_aberrations(api, defocus, cs):
+    w = W.Workload("ab", (20.0, 20.0, 6.0), 30, 128, 3, 2.0, 200.0, 25.0, 4, 2.0, 40, f=(2,),
+                   defocus=defocus, cs=cs)
+    xyz, gauss = W.atoms(w, seed=17)
+    plan = api.Plan.from_workload(w)
+    p, tref = _oracle_trans(w, xyz, gauss)
+    assert p.defocus == defocus and p.cs == cs
+    t = dev(tref, torch.complex64)
+    xy = W.random_positions(w, 9, seed=2)
+    ms = plan.multislice(t, dev(xy), batch=9).cpu().numpy()
+    check_rings(ms, O.multislice_rings(p, tref, xy), FP32_TOL)
+    beams = O.prism_beams(p, 2)
+    sref = O.prism_smatrix(p, tref, beams)
+    for storage, engine, tol in (("f32", "simt", FP32_TOL), ("f16", "tensor", LOWP_TOL)):
+        sm = plan.prism_smatrix(t, 2, storage, batch=32)
+        pr = plan.prism_output(sm, dev(xy), engine=engine).cpu().numpy()
+        check_rings(pr, O.prism_rings(p, sref, beams, 2, xy), tol)
+
+
+# --------------------------------------------- detectors with edges, 4D output
+def test_detector_edges_multislice_and_prism(api):
+    """A BF disc, an annular BF, two ADF rings and a HAADF-like ring."""
+    w, xyz, gauss = _small_prism_case(n=128, f=2)
+    plan = api.Plan.from_workload(w)
+    edges = [0.0, 10.0, 20.0, 41.0, 80.0, 251.0]
+    plan.set_detector_edges(edges)
+    p, tref = _oracle_trans(w, xyz, gauss)
+    t = dev(tref, torch.complex64)
+    xy = W.random_positions(w, 11, seed=6)
+    ms = plan.multislice(t, dev(xy), batch=11).cpu().numpy()
+    assert ms.shape == (11, len(edges) - 1)
+    check_rings(ms, O.multislice_rings(p, tref, xy, edges=edges), FP32_TOL)
+    beams = O.prism_beams(p, 2)
+    sm = plan.prism_smatrix(t, 2, "f32", batch=64)
+    pr = plan.prism_output(sm, dev(xy), engine="simt").cpu().numpy()
+    sref = O.prism_smatrix(p, tref, beams)
+    win = O.prism_window_waves(p, sref, beams, 2, xy)
+    spec = np.abs(np.fft.fft2(win)) ** 2 / (64.0 ** 4)
+    ref = O.detector_rings(O.coarse_ring_table(p, 2, edges), len(edges) - 1, spec)
+    check_rings(pr, ref, FP32_TOL)
+
+
+def _check_dp(got, ref, tol):
+    got = np.asarray(got, np.float64)
+    ref = np.asarray(ref, np.float64)
+    assert np.all(np.isfinite(got))
+    assert np.linalg.norm(got - ref) <= tol * np.linalg.norm(ref)
+    assert np.max(np.abs(got - ref)) <= tol * np.max(ref)
+
+
+def test_multislice_4d_vs_oracle(api):
+    w = W.Workload("d", (20.0, 24.0, 6.0), 30, 128, 3, 2.0, 200.0, 25.0, 4, 2.0, 40)
+    xyz, gauss = W.atoms(w, seed=23)
+    plan = api.Plan.from_workload(w)
+    p, tref = _oracle_trans(w, xyz, gauss)
+    xy = W.random_positions(w, 5, seed=3)
+    dp = plan.multislice_4d(dev(tref, torch.complex64), dev(xy), batch=3).cpu().numpy()
+    _check_dp(dp, O.multislice_dp(p, tref, xy), FP32_TOL)
+
+
+@pytest.mark.parametrize("storage,engine,tol", [("f32", "simt", FP32_TOL), ("bf16", "tensor", LOWP_TOL)])
+def test_prism_4d_vs_oracle(api, storage, engine, tol):
+    w, xyz, gauss = _small_prism_case(n=128, f=4)
+    plan = api.Plan.from_workload(w)
+    p, tref = _oracle_trans(w, xyz, gauss)
+    beams = O.prism_beams(p, 4)
+    sm = plan.prism_smatrix(dev(tref, torch.complex64), 4, storage, batch=32)
+    xy = W.random_positions(w, 7, seed=5)
+    dp = plan.prism_output_4d(sm, dev(xy), chunk=4, engine=engine).cpu().numpy()
+    _check_dp(dp, O.prism_dp(p, O.prism_smatrix(p, tref, beams), beams, 4, xy), tol)

@@ -91,6 +91,16 @@ def _ms_last_slice_unpropagated(p, trans, psi):
             return O.bandlimit_mask(p.n) * np.fft.fft2(trans[s] * psi, axes=(-2, -1))
 
 
+def _chi_defocus_flipped(p, kx, ky):
+    k2 = kx * kx + ky * ky
+    return -math.pi * p.lam * p.defocus * k2 + 0.5 * math.pi * p.cs * p.lam ** 3 * k2 * k2
+
+
+def _chi_cs_no_lambda_cubed(p, kx, ky):
+    k2 = kx * kx + ky * ky
+    return math.pi * p.lam * p.defocus * k2 + 0.5 * math.pi * p.cs * p.lam * k2 * k2
+
+
 CASES = [
     ("propagator", _prop_flipped, [pins.test_phase_grating_one_slice_jacobi_anger,
                                    pins.test_gaussian_beam_fresnel_closed_form]),
@@ -105,6 +115,8 @@ CASES = [
     ("projected_potential", _potential_one_gaussian, [pins.test_potential_sum_rule_and_peak]),
     ("wavelength", _lambda_nonrel, [pins.test_wavelength_textbook_values]),
     ("multislice_k", _ms_last_slice_unpropagated, [pins.test_phase_grating_one_slice_jacobi_anger]),
+    ("aberration_chi", _chi_defocus_flipped, [pins.test_defocus_equals_free_propagation]),
+    ("aberration_chi", _chi_cs_no_lambda_cubed, [pins.test_spherical_aberration_hand_value]),
 ]
 
 

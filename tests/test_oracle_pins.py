@@ -346,3 +346,78 @@ def test_prism_window_origin():
     xy = np.array([[0.0, 0.0], [0.125, 0.124], [15.9, 8.0]])   # dx = 0.25
     org = O.prism_window_origin(p, 4, xy)        # W = 16
     assert org.tolist() == [[56, 56], [57, 56], [(64 - 8) % 64, 24]]
+
+
+# -------------------------------------------------------------- aberrations
+def test_defocus_equals_free_propagation():
+    """A probe with defocus C1 is the in-focus probe propagated by C1 with Eq. 2's
+    propagator (a different code path of the oracle)."""
+    p0 = O.Params((20.0, 24.0, 10.0), 128, 1, 37.0, 200.0, 25.0, 1.0, 30)
+    p1 = O.Params((20.0, 24.0, 10.0), 128, 1, 37.0, 200.0, 25.0, 1.0, 30, defocus=37.0)
+    xy = np.array([[3.1, 17.4]])
+    got = O.probe_k(p1, xy)[0]
+    want = O.probe_k(p0, xy)[0] * O.propagator(p0)      # propagate by dz = 37 A = C1
+    assert np.max(np.abs(got - want)) < 1e-13
+
+
+def test_spherical_aberration_hand_value():
+    """Cs = 1 mm at 200 keV: chi at k = 0.5 1/A is (pi/2) Cs lambda^3 k^4
+    = (pi/2) * 1e7 * 0.0250793^3 * 0.0625 = 15.486 rad (worked by hand)."""
+    p = O.Params((20.0, 20.0, 10.0), 128, 1, 1.0, 200.0, 30.0, 1.0, 30, cs=1e7)
+    assert O.aberration_chi(p, 0.5, 0.0) == pytest.approx(15.486, abs=2e-3)
+    assert O.aberration_chi(p, 0.3, 0.4) == pytest.approx(15.486, abs=2e-3)   # depends on |k| only
+
+
+def test_prism_f1_equals_multislice_with_aberrations():
+    p = O.Params((8.0, 8.0, 6.0), 32, 3, 2.0, 200.0, 30.0, 4.0, 40, defocus=50.0, cs=2e6)
+    rng = np.random.default_rng(9)
+    t = O.transmission(p, rng.random((3, 32, 32)) * 80.0)
+    xy = np.array([[0.3, 0.7], [4.4, 2.25]])
+    beams = O.prism_beams(p, 1)
+    ms = O.multislice_rings(p, t, xy)
+    pr = O.prism_rings(p, O.prism_smatrix(p, t, beams), beams, 1, xy)
+    assert np.max(np.abs(ms - pr)) < 1e-12
+    # and the aberration changes the result
+    p0 = O.Params((8.0, 8.0, 6.0), 32, 3, 2.0, 200.0, 30.0, 4.0, 40)
+    assert np.max(np.abs(ms - O.multislice_rings(p0, t, xy))) > 1e-4
+
+
+# ------------------------------------------------------ detectors, 4D output
+def test_detector_edges_free_space_closed_form():
+    """Annular detectors with arbitrary edges at V = 0: each holds the fraction of
+    aperture pixels whose angle falls in it (counted point by point)."""
+    p = O.Params((16.0, 20.0, 20.0), 64, 2, 5.0, 80.0, 20.0, 2.0, 40)
+    edges = [0.0, 7.5, 13.25, 20.0, 41.0, 60.0]
+    t = np.ones((2, 64, 64), complex)
+    rings = O.multislice_rings(p, t, np.array([[1.0, 2.0]]), edges=edges)[0]
+    counts = np.zeros(len(edges) - 1)
+    n_ap = 0
+    for a in range(-32, 32):
+        for b in range(-32, 32):
+            if 9 * (a * a + b * b) > 64 * 64:
+                continue
+            ang = p.lam * math.sqrt((a / 16.0) ** 2 + (b / 20.0) ** 2) * 1000.0
+            if ang <= 20.0:
+                n_ap += 1
+                for i in range(len(edges) - 1):
+                    if edges[i] <= ang < edges[i + 1]:
+                        counts[i] += 1
+    assert np.max(np.abs(rings - counts / n_ap)) < 1e-13
+    assert rings[3:].sum() == pytest.approx(0.0, abs=1e-15)     # dark field is dark in vacuum
+
+
+def test_4d_output_free_space_and_ring_sums():
+    """V = 0: the diffraction pattern is 1/|A| on aperture pixels and 0 elsewhere;
+    with a specimen, summing the pattern over a ring gives that ring's output."""
+    p = O.Params((16.0, 16.0, 8.0), 64, 2, 4.0, 200.0, 25.0, 2.0, 40)
+    xy = np.array([[3.3, 1.1], [9.0, 12.5]])
+    dp0 = O.multislice_dp(p, np.ones((2, 64, 64), complex), xy)
+    ap = O.aperture(p)
+    assert np.max(np.abs(dp0 - ap[None] / ap.sum())) < 1e-14
+    rng = np.random.default_rng(8)
+    t = O.transmission(p, rng.random((2, 64, 64)) * 70.0)
+    dp = O.multislice_dp(p, t, xy)
+    rings = O.multislice_rings(p, t, xy)
+    table = O.ring_table(p)
+    for i in (0, 5, 17):
+        assert np.allclose(dp[:, table == i].sum(axis=1), rings[:, i], rtol=1e-12, atol=1e-16)

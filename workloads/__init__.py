@@ -44,6 +44,8 @@ class Workload:
     f: Tuple[int, ...] = ()            # PRISM interpolation factors exercised
     fp_configs: int = 1                # frozen-phonon configurations
     fp_sigma: float = 0.0              # per-axis displacement std (A)
+    defocus: float = 0.0               # probe defocus C1 (A)
+    cs: float = 0.0                    # spherical aberration Cs (A)
 
     @property
     def n_probes(self) -> int:

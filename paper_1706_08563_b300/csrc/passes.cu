@@ -220,7 +220,14 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, ColCfg<N>::MINB) k_col_pas
         const uint16_t l = __ldg(a.lut + (size_t)ky * N + col);
         float2 val = make_float2(0.0f, 0.0f);
         if (l & kLutAperture) {
-          double th = thx + (double)signed_freq(ky, N) * yp * a.inv_ly;
+          const int n = signed_freq(ky, N);
+          double th = thx + (double)n * yp * a.inv_ly;
+          if (a.chi_c1 != 0.0 || a.chi_c3 != 0.0) {
+            // aberrations exp(-i chi(k)), chi / (2 pi) = chi_c1 |k|^2 + chi_c3 |k|^4
+            const double kx = (double)signed_freq(col, N) * a.inv_lx, kyy = (double)n * a.inv_ly;
+            const double k2 = kx * kx + kyy * kyy;
+            th += a.chi_c1 * k2 + a.chi_c3 * k2 * k2;
+          }
           th -= rint(th);
           float s, cth;
           sincospif(-2.0f * (float)th, &s, &cth);
@@ -245,7 +252,7 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, ColCfg<N>::MINB) k_col_pas
     }
 #endif
 
-    if constexpr (MODE == COL_SLICE || MODE == COL_DET || MODE == COL_FFT)
+    if constexpr (MODE == COL_SLICE || MODE == COL_DET || MODE == COL_FFT || MODE == COL_DP)
       fft_dist<N, false>(v, view, t, sync, tw);
 
     if constexpr (MODE == COL_SLICE) {

@@ -121,8 +121,14 @@ __global__ void k_pot_fill(const int* __restrict__ key, int64_t n_atoms, const i
 }
 
 // Sum over periodic images of the two Gaussians along one axis (pixel units).
-__device__ __forceinline__ void axis_terms(float d0, float rc, float e1, float e2, int n, float& g1, float& g2) {
-  d0 -= (float)n * rintf(d0 / (float)n);
+// dj = pixel index - atom pixel index (integer), f = the atom's fractional
+// offset.  The integer offset is wrapped into [-n/2, n/2) before f is taken off,
+// so that f keeps its full FP32 precision next to the cell edge.
+__device__ __forceinline__ void axis_terms(int dj, float f, float rc, float e1, float e2, int n, float& g1,
+                                           float& g2) {
+  if (dj >= n / 2) dj -= n;
+  if (dj < -(n / 2)) dj += n;
+  const float d0 = (float)dj - f;
   g1 = 0.0f;
   g2 = 0.0f;
   const int kmax = (int)ceilf(rc / (float)n);
@@ -163,13 +169,13 @@ __global__ void __launch_bounds__(kPotThreads) k_potential(const AtomRec* __rest
         for (int idx = b; idx < e; ++idx) {
           const AtomRec at = recs[__ldg(sorted + idx)];
           float gx1, gx2;
-          axis_terms((float)(j - at.jx) - at.fx, at.rcx, at.e1x, at.e2x, n, gx1, gx2);
+          axis_terms(j - at.jx, at.fx, at.rcx, at.e1x, at.e2x, n, gx1, gx2);
           if (gx1 == 0.0f && gx2 == 0.0f) continue;
 #pragma unroll
           for (int q = 0; q < PX; ++q) {
             const int i = i0 + q * (kPotThreads / kTile);
             float gy1, gy2;
-            axis_terms((float)(i - at.iy) - at.fy, at.rcy, at.e1y, at.e2y, n, gy1, gy2);
+            axis_terms(i - at.iy, at.fy, at.rcy, at.e1y, at.e2y, n, gy1, gy2);
             const float v = at.a1 * gx1 * gy1 + at.a2 * gx2 * gy2;
             acc[q] += __float2ll_rn(v * kFix);
           }

@@ -1,15 +1,6 @@
 """CUDA path (through the C ABI) vs the FP64 oracle, element by element.
 
-Tolerances.  FP32 arithmetic is held to relative L2 <= 1e-4 over the whole
-[probe, ring] array (the benchmark spec's bound), and ring by ring: a ring whose RMS
-is at least FLOOR of the largest ring's RMS must match to relative L2 <= tol;
-a darker ring must match to an absolute RMS error <= tol * FLOOR * (largest
-ring RMS).  Rounding leaves every Fourier pixel with an error set by the bright
-field, not by the ring's own signal, so rings far below the bright field carry
-an error floor that no relative bound can meet (their relative error grows
-like 1/sqrt(I) and then like 1/I).  FLOOR is 1e-5 for FP32 and 1e-4 for
-FP16/BF16 S-matrix storage (tol = 1e-2 there).  Unit kernels (FFT,
-potentials) are held to their FP32 rounding level.
+The ring tolerances and their rationale are in tests/tolerances.py.
 """
 import math
 
@@ -22,29 +13,7 @@ from oracle import stem as O
 
 pytestmark = pytest.mark.gpu
 
-FP32_TOL = 1e-4
-LOWP_TOL = 1e-2
-FP32_FLOOR = 1e-5
-LOWP_FLOOR = 1e-4
-
-
-def rel_l2(a, b):
-    return O.rel_l2(np.asarray(a, np.float64), np.asarray(b, np.float64))
-
-
-def check_rings(got, ref, tol, floor=None):
-    floor = (FP32_FLOOR if tol <= FP32_TOL else LOWP_FLOOR) if floor is None else floor
-    got = np.asarray(got, np.float64)
-    ref = np.asarray(ref, np.float64)
-    assert got.shape == ref.shape
-    assert np.all(np.isfinite(got))
-    assert rel_l2(got, ref) <= tol, rel_l2(got, ref)
-    norms = np.sqrt(np.mean(ref ** 2, axis=0))
-    top = norms.max()
-    for i in range(ref.shape[1]):
-        err = np.sqrt(np.mean((got[:, i] - ref[:, i]) ** 2))
-        bound = tol * max(norms[i], floor * top)
-        assert err <= bound, (i, err / max(norms[i], 1e-300), norms[i] / top)
+from tolerances import FP32_FLOOR, FP32_TOL, LOWP_FLOOR, LOWP_TOL, check_rings, rel_l2  # noqa: F401
 
 
 @pytest.fixture(scope="module")

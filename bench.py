@@ -317,10 +317,27 @@ def measure_multislice(args, dev, hbm, src):
     band = (2 * (w.n // 3) + 1) / w.n
     alg = w.batch * w.n_slices * 32.0 * band * n2 + w.n_slices * 8.0 * n2
     ach = alg / (ms / 1e3) / 1e9
+    # the same launches under the streaming memory model (stack in pinned host memory)
+    host = trans.cpu().pin_memory()
+    ws_s = torch.empty(api._lib.load().stem_multislice_streamed_workspace(plan._h, w.batch), dtype=torch.uint8,
+                       device=dev)
+    for _ in range(2):
+        plan.multislice_streamed(host, xy, batch=w.batch, rings=rings, workspace=ws_s)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(k):
+        plan.multislice_streamed(host, xy, batch=w.batch, rings=rings, workspace=ws_s)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_s = e0.elapsed_time(e1) / k
     return {"workload": w.name, "value": w.batch / (ms / 1e3), "unit": "probes/s", "ms_per_launch": ms,
             "batch": w.batch, "grid": w.n, "slices": w.n_slices,
             "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                         "peak_source": src, "kernel": "k_row_pass/k_col_pass<1024>"}}
+                         "peak_source": src, "kernel": "k_row_pass/k_col_pass<1024>"},
+            "streamed": {"value": w.batch / (ms_s / 1e3), "unit": "probes/s", "ms_per_launch": ms_s,
+                         "footprint_bytes": api.footprint_bytes(w, "ms_streamed", batch=w.batch),
+                         "footprint_bytes_single": api.footprint_bytes(w, "ms", batch=w.batch),
+                         "h2d_bytes_per_launch": w.n_slices * n2 * 8}}
 
 
 def measure_serving(dev, n_requests=40, rate_hz=40.0):

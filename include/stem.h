@@ -183,6 +183,31 @@ stem_status stem_multislice_scan_noalloc(stem_plan plan, const void* trans, cons
                                          float* rings_out, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * Streaming memory model ("Streaming Data for Very Large Simulations"): the
+ * transmission stack stays in HOST memory and only a few slices are on the
+ * device at a time.
+ *   trans_host  complex64 [n_slices][n][n] in host memory (page-locked memory,
+ *               e.g. cudaHostAlloc, lets the copies overlap the passes;
+ *               pageable memory works but the copies then stall the host).
+ *               A device pointer is accepted too (the copies become
+ *               device-to-device).  It must stay valid and unchanged until the
+ *               work queued on `stream` has finished.
+ *   workspace   >= stem_multislice_streamed_workspace(plan, batch) bytes: the
+ *               batch of waves followed by 3 slice buffers of n*n*8 bytes.
+ * Each slice is copied into the next free buffer by an asynchronous copy on a
+ * stream the call creates (ordered after the work already queued on `stream`)
+ * as soon as the row pass that read that buffer's previous slice has
+ * finished; the row pass of a slice waits for its copy.  Every batch of
+ * probes copies all n_slices slices again (the price of the smaller
+ * footprint).  Results equal stem_multislice_scan's.  Calls that overlap on
+ * the GPU must use different workspaces.
+ * ------------------------------------------------------------------------ */
+size_t stem_multislice_streamed_workspace(stem_plan plan, int32_t batch);
+stem_status stem_multislice_scan_streamed(stem_plan plan, const void* trans_host, const double* probe_xy,
+                                          int64_t n_probes, int32_t batch, float weight, float* rings_out,
+                                          void* workspace, size_t workspace_bytes, void* stream);
+
+/* ---------------------------------------------------------------------------
  * PRISM compact S-matrix ("Description of Algorithms", PRISM paragraph;
  * "PRISM Probe Simulations").  Beams: every f-th Fourier component in x and y
  * inside the probe aperture, psi_b(r) = exp(2 pi i k_b . r), ordered by n then
@@ -201,6 +226,17 @@ size_t stem_prism_smatrix_workspace(stem_plan plan, int32_t batch);
 stem_status stem_prism_smatrix(stem_plan plan, const void* trans, int32_t f, stem_storage storage,
                                int32_t batch, void* smatrix, size_t smatrix_bytes,
                                void* workspace, size_t workspace_bytes, void* stream);
+
+/* The S-matrix built under the streaming memory model: trans_host as for
+ * stem_multislice_scan_streamed (host stack, copied slice by slice into 3
+ * device buffers; every batch of beams copies all slices); workspace >=
+ * stem_prism_smatrix_streamed_workspace(plan, batch).  The S-matrix itself is
+ * written to device memory as by stem_prism_smatrix, with identical bytes. */
+size_t stem_prism_smatrix_streamed_workspace(stem_plan plan, int32_t batch);
+stem_status stem_prism_smatrix_streamed(stem_plan plan, const void* trans_host, int32_t f,
+                                        stem_storage storage, int32_t batch, void* smatrix,
+                                        size_t smatrix_bytes, void* workspace, size_t workspace_bytes,
+                                        void* stream);
 
 /* ---------------------------------------------------------------------------
  * PRISM output ("Description of Algorithms", PRISM paragraph; "PRISM Probe
@@ -260,7 +296,10 @@ stem_status stem_fft2(int32_t n, int64_t batch, int32_t inverse, void* data, voi
  * memory estimate of "Streaming Data for Very Large Simulations").
  *   algo 0 = multislice (transmission stack + one batch of waves + rings),
  *   algo 1 = PRISM (transmission stack + S-matrix + S-matrix workspace +
- *            output workspace for chunks of up to 4096 probes + rings)
+ *            output workspace for chunks of up to 4096 probes + rings),
+ *   algo 2 = multislice, streamed (3 slice buffers instead of the stack),
+ *   algo 3 = PRISM with the S-matrix built streamed (3 slice buffers instead
+ *            of the stack; the S-matrix itself stays resident)
  * ------------------------------------------------------------------------ */
 size_t stem_footprint_bytes(const stem_params* params, int32_t algo, int32_t f,
                             stem_storage storage, int64_t n_probes, int32_t batch);

@@ -52,6 +52,12 @@ SIGNATURES = {
                                        c_void_p, c_size_t, c_void_p]),
     "stem_multislice_scan_noalloc": (c_int32, [c_void_p, c_void_p, c_void_p, c_int64, c_int32, c_float,
                                                c_void_p, c_void_p]),
+    "stem_multislice_streamed_workspace": (c_size_t, [c_void_p, c_int32]),
+    "stem_multislice_scan_streamed": (c_int32, [c_void_p, c_void_p, c_void_p, c_int64, c_int32, c_float,
+                                                c_void_p, c_void_p, c_size_t, c_void_p]),
+    "stem_prism_smatrix_streamed_workspace": (c_size_t, [c_void_p, c_int32]),
+    "stem_prism_smatrix_streamed": (c_int32, [c_void_p, c_void_p, c_int32, c_int32, c_int32, c_void_p, c_size_t,
+                                              c_void_p, c_size_t, c_void_p]),
     "stem_multislice_scan_4d": (c_int32, [c_void_p, c_void_p, c_void_p, c_int64, c_int32, c_float, c_void_p,
                                           c_void_p, c_size_t, c_void_p]),
     "stem_prism_output_4d": (c_int32, [c_void_p, c_int32, c_int32, c_int32, c_void_p, c_void_p, c_int64, c_int32,

@@ -36,6 +36,18 @@ def _need(t: torch.Tensor, dtype: torch.dtype, name: str, shape=None) -> torch.T
     return t.contiguous()
 
 
+def _need_host(t: torch.Tensor, dtype: torch.dtype, name: str, shape=None) -> torch.Tensor:
+    """A host tensor for the streaming memory model (page-locked memory lets the
+    copies overlap the passes; a pageable tensor works, slower)."""
+    if not isinstance(t, torch.Tensor) or t.is_cuda:
+        raise ValueError(f"{name} must be a host (CPU) tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    return t.contiguous()
+
+
 def _workspace(nbytes: int, device) -> torch.Tensor:
     return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
 
@@ -151,6 +163,29 @@ class Plan:
               "stem_multislice_scan")
         return rings
 
+    def multislice_streamed(self, trans_host: torch.Tensor, probe_xy: torch.Tensor, batch: int = 256,
+                            rings: Optional[torch.Tensor] = None, weight: float = 1.0,
+                            workspace: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """Multislice under the streaming memory model: the transmission stack
+        stays in host memory (pin it for overlap) and three slice buffers cycle
+        on the device.  The host tensor must not change until the call's work
+        on the current stream has finished."""
+        lib = _lib.load()
+        trans_host = _need_host(trans_host, torch.complex64, "trans_host", (self.n_slices, self.n, self.n))
+        probe_xy = _need(probe_xy, torch.float64, "probe_xy")
+        npr = probe_xy.shape[0]
+        if rings is None:
+            rings = torch.zeros((npr, self.n_rings), dtype=torch.float32, device=self.device)
+        else:
+            rings = _need(rings, torch.float32, "rings", (npr, self.n_rings))
+        batch = int(max(1, min(batch, max(npr, 1))))
+        ws = workspace if workspace is not None else _workspace(
+            lib.stem_multislice_streamed_workspace(self._h, batch), self.device)
+        check(lib.stem_multislice_scan_streamed(self._h, trans_host.data_ptr(), _ptr(probe_xy), npr, batch,
+                                                float(weight), _ptr(rings), _ptr(ws), ws.numel(),
+                                                _stream(self.device)), "stem_multislice_scan_streamed")
+        return rings
+
     def multislice_4d(self, trans: torch.Tensor, probe_xy: torch.Tensor, batch: int = 64,
                       dp: Optional[torch.Tensor] = None, weight: float = 1.0,
                       workspace: Optional[torch.Tensor] = None) -> torch.Tensor:
@@ -202,6 +237,27 @@ class Plan:
             lib.stem_prism_smatrix_workspace(self._h, batch), self.device)
         check(lib.stem_prism_smatrix(self._h, _ptr(trans), f, st, batch, _ptr(buf), buf.numel(), _ptr(ws),
                                      ws.numel(), _stream(self.device)), "stem_prism_smatrix")
+        nbp = (nb + 63) // 64 * 64
+        return SMatrix(buf, f, storage, nb, nbp, (nbp * 4 + 255) // 256 * 256, self.n)
+
+    def prism_smatrix_streamed(self, trans_host: torch.Tensor, f: int, storage: str = "f32", batch: int = 128,
+                               workspace: Optional[torch.Tensor] = None,
+                               out: Optional[torch.Tensor] = None) -> SMatrix:
+        """The S-matrix built with the transmission stack streamed from host memory."""
+        lib = _lib.load()
+        trans_host = _need_host(trans_host, torch.complex64, "trans_host", (self.n_slices, self.n, self.n))
+        st = STORAGE[storage]
+        nbytes = lib.stem_prism_smatrix_bytes(self._h, f, st)
+        if nbytes == 0:
+            raise ValueError(f"unsupported f={f} or storage={storage}")
+        nb = len(self.prism_beams(f))
+        batch = int(max(1, min(batch, nb)))
+        buf = out if out is not None else torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        ws = workspace if workspace is not None else _workspace(
+            lib.stem_prism_smatrix_streamed_workspace(self._h, batch), self.device)
+        check(lib.stem_prism_smatrix_streamed(self._h, trans_host.data_ptr(), f, st, batch, _ptr(buf), buf.numel(),
+                                              _ptr(ws), ws.numel(), _stream(self.device)),
+              "stem_prism_smatrix_streamed")
         nbp = (nb + 63) // 64 * 64
         return SMatrix(buf, f, storage, nb, nbp, (nbp * 4 + 255) // 256 * 256, self.n)
 
@@ -279,11 +335,25 @@ def fft2(x: torch.Tensor, inverse: bool = False) -> torch.Tensor:
     return x
 
 
+ALGO = {"ms": 0, "prism": 1, "ms_streamed": 2, "prism_streamed": 3}
+
+
 def footprint_bytes(w, algo: str = "ms", f: int = 1, storage: str = "f32", batch: int = 256) -> int:
-    """Device bytes a simulation of workload ``w`` needs (admission control)."""
+    """Device bytes a simulation of workload ``w`` needs (admission control).
+    algo: "ms", "prism", or their "_streamed" forms (transmission stack in host memory)."""
     lib = _lib.load()
     p = StemParams((ctypes.c_double * 3)(*[float(c) for c in w.cell]), int(w.n), int(w.n_slices),
                    float(w.slice_dz), float(w.energy_kev), float(w.alpha_mrad), float(w.ring_width_mrad),
                    int(w.n_rings), float(getattr(w, "defocus", 0.0)), float(getattr(w, "cs", 0.0)))
-    return int(lib.stem_footprint_bytes(ctypes.byref(p), 0 if algo == "ms" else 1, f, STORAGE[storage],
-                                        w.n_probes, batch))
+    return int(lib.stem_footprint_bytes(ctypes.byref(p), ALGO[algo], f, STORAGE[storage], w.n_probes, batch))
+
+
+def memory_model(w, algo: str, budget_bytes: int, f: int = 1, storage: str = "f32", batch: int = 256) -> str:
+    """The paper's automatic choice between the single-transfer and the
+    streaming memory model: "single" if the resident footprint fits the
+    budget, else "streamed" if that fits, else raise MemoryError."""
+    if footprint_bytes(w, algo, f, storage, batch) <= budget_bytes:
+        return "single"
+    if footprint_bytes(w, algo + "_streamed", f, storage, batch) <= budget_bytes:
+        return "streamed"
+    raise MemoryError(f"{w.name}: needs more than {budget_bytes} device bytes even when streamed")

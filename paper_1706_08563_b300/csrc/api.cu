@@ -9,6 +9,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstring>
+#include <memory>
 #include <new>
 
 #include "internal.h"
@@ -44,6 +45,84 @@ int log2i(int n) {
 }
 
 cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
+
+constexpr int kStreamBufs = 3;
+
+// Supplies the transmission function t_n to a slice loop.
+//
+// Resident: a pointer into the device stack [S][n][n].
+// Streamed (the paper's streaming memory model, "Streaming Data for Very Large
+// Simulations"): the stack stays in host memory and kStreamBufs slice buffers
+// take turns.  Each buffer is refilled by an asynchronous copy on a second
+// stream as soon as the row pass that read it has finished, so the copies of
+// the next slices run while the passes of the current one do.  The stream and
+// events live for one call; destroying them with work still queued is allowed
+// (CUDA releases them when that work completes).
+class SliceSource {
+ public:
+  SliceSource(const float2* device_stack, size_t plane) : dev_(device_stack), plane_(plane) {}
+  SliceSource(const float2* host_stack, size_t plane, float2* bufs) : host_(host_stack), plane_(plane) {
+    for (int k = 0; k < kStreamBufs; ++k) buf_[k] = bufs + k * plane;
+  }
+  SliceSource(const SliceSource&) = delete;
+  SliceSource& operator=(const SliceSource&) = delete;
+  ~SliceSource() {
+    if (copy_) cudaStreamDestroy(copy_);
+    for (cudaEvent_t ev : ready_) if (ev) cudaEventDestroy(ev);
+    for (cudaEvent_t ev : done_) if (ev) cudaEventDestroy(ev);
+    if (start_) cudaEventDestroy(start_);
+  }
+
+  // Streamed: make the copy stream start after the work already queued on s
+  // (an earlier call may still read the buffers).
+  cudaError_t begin(cudaStream_t s) {
+    if (!host_) return cudaSuccess;
+    cudaError_t e = cudaStreamCreateWithFlags(&copy_, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&start_, cudaEventDisableTiming);
+    for (int k = 0; k < kStreamBufs && e == cudaSuccess; ++k) {
+      e = cudaEventCreateWithFlags(&ready_[k], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&done_[k], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(start_, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(copy_, start_, 0);
+    return e;
+  }
+
+  // t_n for the next row pass, ordered before it on s.
+  cudaError_t acquire(int slice, cudaStream_t s, const float2** t) {
+    if (!host_) {
+      *t = dev_ + (size_t)slice * plane_;
+      return cudaSuccess;
+    }
+    const int k = (int)(step_ % kStreamBufs);
+    cudaError_t e = cudaSuccess;
+    if (step_ >= kStreamBufs) e = cudaStreamWaitEvent(copy_, done_[k], 0);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(buf_[k], host_ + (size_t)slice * plane_, plane_ * sizeof(float2), cudaMemcpyDefault, copy_);
+    if (e == cudaSuccess) e = cudaEventRecord(ready_[k], copy_);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ready_[k], 0);
+    *t = buf_[k];
+    return e;
+  }
+
+  // After the row pass that read the buffer has been queued on s.
+  cudaError_t release(cudaStream_t s) {
+    if (!host_) return cudaSuccess;
+    const int k = (int)(step_++ % kStreamBufs);
+    return cudaEventRecord(done_[k], s);
+  }
+
+ private:
+  const float2* dev_ = nullptr;
+  const float2* host_ = nullptr;
+  size_t plane_ = 0;
+  float2* buf_[kStreamBufs] = {};
+  cudaStream_t copy_ = nullptr;
+  cudaEvent_t start_ = nullptr;
+  cudaEvent_t ready_[kStreamBufs] = {};
+  cudaEvent_t done_[kStreamBufs] = {};
+  int64_t step_ = 0;
+};
 
 stem_status cuda_status(cudaError_t e) { return e == cudaSuccess ? STEM_OK : STEM_ERR_CUDA; }
 
@@ -206,7 +285,6 @@ stem_status stem_plan_create(const stem_params* params, stem_plan* out) {
   for (int lf = 0; lf <= kMaxLog2F; ++lf) {
     const int f = 1 << lf;
     if (f > n / 8) break;
-    const int w = n / f;
     const std::vector<uint16_t> coarse = coarse_lut(lut, n, f);
     upload(reinterpret_cast<void**>(&pl->lut[lf]), coarse.data(), coarse.size() * sizeof(uint16_t));
     // PRISM beams: aperture pixels on every f-th frequency, ordered by n then m.
@@ -307,17 +385,24 @@ size_t stem_multislice_workspace(stem_plan pl, int32_t batch) {
 // The slice loop of Eq. 1 and Eq. 2 over batches of probes; the last column
 // pass bins |Psi_hat|^2 into rings (dp == NULL) or accumulates the whole
 // diffraction pattern into dp.
-static stem_status run_multislice(stem_plan pl, const void* trans, const double* probe_xy, int64_t n_probes,
-                                  int32_t batch, float weight, float* rings_out, float* dp_out, void* ws,
-                                  size_t ws_bytes, void* stream) {
+static stem_status run_multislice(stem_plan pl, const void* trans, bool streamed, const double* probe_xy,
+                                  int64_t n_probes, int32_t batch, float weight, float* rings_out, float* dp_out,
+                                  void* ws, size_t ws_bytes, void* stream) {
   if (!pl || !trans || n_probes < 0 || (n_probes > 0 && (!probe_xy || (!rings_out && !dp_out))) || batch < 1 ||
       batch > 65535 || !ws)
     return STEM_ERR_INVALID;
   const int n = pl->n;
   if (n < 64) return STEM_ERR_UNSUPPORTED;
-  if (ws_bytes < stem_multislice_workspace(pl, batch)) return STEM_ERR_NOMEM;
+  const size_t waves = stem_multislice_workspace(pl, batch);
+  if (ws_bytes < (streamed ? stem_multislice_streamed_workspace(pl, batch) : waves)) return STEM_ERR_NOMEM;
   cudaStream_t s = as_stream(stream);
   const size_t plane = (size_t)n * n;
+  const float2* t = static_cast<const float2*>(trans);
+  float2* bufs = reinterpret_cast<float2*>(static_cast<char*>(ws) + waves);
+  std::unique_ptr<SliceSource> src(streamed ? new (std::nothrow) SliceSource(t, plane, bufs)
+                                             : new (std::nothrow) SliceSource(t, plane));
+  if (!src) return STEM_ERR_NOMEM;
+  if (n_probes > 0 && src->begin(s) != cudaSuccess) return STEM_ERR_CUDA;
   PassArgs a;
   a.wave = static_cast<float2*>(ws);
   a.prop_x = pl->prop_x;
@@ -332,7 +417,6 @@ static stem_status run_multislice(stem_plan pl, const void* trans, const double*
   a.band = 1;   // the last column pass reads waves whose out-of-band columns were never written
   a.chi_c1 = 0.5 * pl->lam * pl->p.defocus_a;
   a.chi_c3 = 0.25 * pl->p.cs_a * pl->lam * pl->lam * pl->lam;
-  const float2* t = static_cast<const float2*>(trans);
   const int last = dp_out ? COL_DP : COL_DET;
   for (int64_t p0 = 0; p0 < n_probes; p0 += batch) {
     a.batch = (int)std::min<int64_t>(batch, n_probes - p0);
@@ -341,8 +425,9 @@ static stem_status run_multislice(stem_plan pl, const void* trans, const double*
     if (dp_out) a.dp = dp_out + p0 * plane;
     cudaError_t e = launch_col_pass(n, COL_PROBE_INIT, a, s);
     for (int sl = 0; sl < pl->p.n_slices && e == cudaSuccess; ++sl) {
-      a.trans = t + sl * plane;
-      e = launch_row_pass(n, ROW_SLICE, a, s);
+      e = src->acquire(sl, s, &a.trans);
+      if (e == cudaSuccess) e = launch_row_pass(n, ROW_SLICE, a, s);
+      if (e == cudaSuccess) e = src->release(s);
       if (e == cudaSuccess) e = launch_col_pass(n, sl + 1 < pl->p.n_slices ? COL_SLICE : last, a, s);
     }
     if (e != cudaSuccess) return STEM_ERR_CUDA;
@@ -354,14 +439,27 @@ stem_status stem_multislice_scan(stem_plan pl, const void* trans, const double* 
                                  int32_t batch, float weight, float* rings_out, void* ws, size_t ws_bytes,
                                  void* stream) {
   if (n_probes > 0 && !rings_out) return STEM_ERR_INVALID;
-  return run_multislice(pl, trans, probe_xy, n_probes, batch, weight, rings_out, nullptr, ws, ws_bytes, stream);
+  return run_multislice(pl, trans, false, probe_xy, n_probes, batch, weight, rings_out, nullptr, ws, ws_bytes, stream);
+}
+
+size_t stem_multislice_streamed_workspace(stem_plan pl, int32_t batch) {
+  if (!pl || batch < 1) return 0;
+  return stem_multislice_workspace(pl, batch) + (size_t)kStreamBufs * pl->n * pl->n * sizeof(float2);
+}
+
+stem_status stem_multislice_scan_streamed(stem_plan pl, const void* trans_host, const double* probe_xy,
+                                          int64_t n_probes, int32_t batch, float weight, float* rings_out, void* ws,
+                                          size_t ws_bytes, void* stream) {
+  if (n_probes > 0 && !rings_out) return STEM_ERR_INVALID;
+  return run_multislice(pl, trans_host, true, probe_xy, n_probes, batch, weight, rings_out, nullptr, ws, ws_bytes,
+                        stream);
 }
 
 stem_status stem_multislice_scan_4d(stem_plan pl, const void* trans, const double* probe_xy, int64_t n_probes,
                                     int32_t batch, float weight, float* dp_out, void* ws, size_t ws_bytes,
                                     void* stream) {
   if (n_probes > 0 && !dp_out) return STEM_ERR_INVALID;
-  return run_multislice(pl, trans, probe_xy, n_probes, batch, weight, nullptr, dp_out, ws, ws_bytes, stream);
+  return run_multislice(pl, trans, false, probe_xy, n_probes, batch, weight, nullptr, dp_out, ws, ws_bytes, stream);
 }
 
 // ----------------------------------------------------------------------------- PRISM S-matrix
@@ -389,8 +487,15 @@ size_t stem_prism_smatrix_workspace(stem_plan pl, int32_t batch) {
   return smatrix_ws_waves(pl->n, batch) + (size_t)batch * sizeof(unsigned);
 }
 
-stem_status stem_prism_smatrix(stem_plan pl, const void* trans, int32_t f, stem_storage storage, int32_t batch,
-                               void* smatrix, size_t smatrix_bytes, void* ws, size_t ws_bytes, void* stream) {
+size_t stem_prism_smatrix_streamed_workspace(stem_plan pl, int32_t batch) {
+  if (!pl || batch < 1) return 0;
+  return (stem_prism_smatrix_workspace(pl, batch) + 255) / 256 * 256 +
+         (size_t)kStreamBufs * pl->n * pl->n * sizeof(float2);
+}
+
+static stem_status run_smatrix(stem_plan pl, const void* trans, bool streamed, int32_t f, stem_storage storage,
+                               int32_t batch, void* smatrix, size_t smatrix_bytes, void* ws, size_t ws_bytes,
+                               void* stream) {
   if (!pl || !trans || !smatrix || !ws || !f_ok(pl, f) || storage < STEM_F32 || storage > STEM_BF16 || batch < 1 ||
       batch > 65535)
     return STEM_ERR_INVALID;
@@ -399,24 +504,32 @@ stem_status stem_prism_smatrix(stem_plan pl, const void* trans, int32_t f, stem_
   const int lf = log2i(f);
   const int nb = pl->n_beams[lf];
   const SmatLayout L = smatrix_layout(n, nb, storage);
-  if (smatrix_bytes < L.total || ws_bytes < stem_prism_smatrix_workspace(pl, batch)) return STEM_ERR_NOMEM;
+  const size_t need = streamed ? stem_prism_smatrix_streamed_workspace(pl, batch) : stem_prism_smatrix_workspace(pl, batch);
+  if (smatrix_bytes < L.total || ws_bytes < need) return STEM_ERR_NOMEM;
   if (reinterpret_cast<uintptr_t>(smatrix) % 256) return STEM_ERR_INVALID;
   cudaStream_t s = as_stream(stream);
   const size_t plane = (size_t)n * n;
+  const float2* t = static_cast<const float2*>(trans);
+  float2* bufs = reinterpret_cast<float2*>(static_cast<char*>(ws) +
+                                           (stem_prism_smatrix_workspace(pl, batch) + 255) / 256 * 256);
+  std::unique_ptr<SliceSource> src(streamed ? new (std::nothrow) SliceSource(t, plane, bufs)
+                                             : new (std::nothrow) SliceSource(t, plane));
+  if (!src) return STEM_ERR_NOMEM;
+  if (src->begin(s) != cudaSuccess) return STEM_ERR_CUDA;
   PassArgs a;
   a.wave = static_cast<float2*>(ws);
   a.prop_x = pl->prop_x;
   a.prop_y = pl->prop_y;
   a.prop_scale = 1.0f / (float)plane;
   a.beam_max = reinterpret_cast<unsigned*>(static_cast<char*>(ws) + smatrix_ws_waves(n, batch));
-  const float2* t = static_cast<const float2*>(trans);
   for (int b0 = 0; b0 < nb; b0 += batch) {
     a.batch = std::min(batch, nb - b0);
     a.beams = pl->beams[lf] + b0;
     cudaError_t e = cudaMemsetAsync(a.beam_max, 0, a.batch * sizeof(unsigned), s);
     for (int sl = 0; sl < pl->p.n_slices && e == cudaSuccess; ++sl) {
-      a.trans = t + sl * plane;
-      e = launch_row_pass(n, sl == 0 ? ROW_BEAM0 : ROW_SLICE, a, s);
+      e = src->acquire(sl, s, &a.trans);
+      if (e == cudaSuccess) e = launch_row_pass(n, sl == 0 ? ROW_BEAM0 : ROW_SLICE, a, s);
+      if (e == cudaSuccess) e = src->release(s);
       if (e == cudaSuccess) e = launch_col_pass(n, COL_SLICE, a, s);
     }
     if (e == cudaSuccess) e = launch_row_pass(n, ROW_IFFT_MAX, a, s);
@@ -424,6 +537,17 @@ stem_status stem_prism_smatrix(stem_plan pl, const void* trans, int32_t f, stem_
     if (e != cudaSuccess) return STEM_ERR_CUDA;
   }
   return STEM_OK;
+}
+
+stem_status stem_prism_smatrix(stem_plan pl, const void* trans, int32_t f, stem_storage storage, int32_t batch,
+                               void* smatrix, size_t smatrix_bytes, void* ws, size_t ws_bytes, void* stream) {
+  return run_smatrix(pl, trans, false, f, storage, batch, smatrix, smatrix_bytes, ws, ws_bytes, stream);
+}
+
+stem_status stem_prism_smatrix_streamed(stem_plan pl, const void* trans_host, int32_t f, stem_storage storage,
+                                        int32_t batch, void* smatrix, size_t smatrix_bytes, void* ws,
+                                        size_t ws_bytes, void* stream) {
+  return run_smatrix(pl, trans_host, true, f, storage, batch, smatrix, smatrix_bytes, ws, ws_bytes, stream);
 }
 
 // ----------------------------------------------------------------------------- PRISM output
@@ -554,12 +678,14 @@ size_t stem_footprint_bytes(const stem_params* p, int32_t algo, int32_t f, stem_
   const size_t n = (size_t)p->n, plane = n * n;
   const size_t trans = (size_t)p->n_slices * plane * sizeof(float2);
   const size_t rings = (size_t)std::max<int64_t>(n_probes, 0) * p->n_rings * sizeof(float);
-  if (algo == 0) return trans + (size_t)batch * plane * sizeof(float2) + rings;
+  if (algo < 0 || algo > 3) return 0;
+  const size_t stack = algo >= 2 ? (size_t)kStreamBufs * plane * sizeof(float2) : trans;
+  if (algo == 0 || algo == 2) return stack + (size_t)batch * plane * sizeof(float2) + rings;
   if (!is_pow2(f) || f > p->n / 8) return 0;
   const int nb = count_beams(p, f, wavelength_a(p->energy_kev));
   const SmatLayout L = smatrix_layout(p->n, nb, storage);
   const int chunk = (int)std::min<int64_t>(std::max<int64_t>(n_probes, 1), 4096);
-  return trans + L.total + (size_t)batch * plane * sizeof(float2) + (size_t)batch * 4 +
+  return stack + L.total + (size_t)batch * plane * sizeof(float2) + (size_t)batch * 4 +
          output_workspace_layout(p->n, f, chunk, L.nbp).total + rings;
 }
 

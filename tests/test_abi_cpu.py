@@ -93,3 +93,40 @@ def test_footprint_prism_counts_the_beams():
     assert f1 > f4 > 0
     assert h16 < f1
     assert lib.stem_footprint_bytes(ctypes.byref(p), 1, 3, 0, 4096, 64) == 0   # f not a power of two
+
+
+def test_footprint_streamed_replaces_the_stack_by_three_slices():
+    lib = _lib.load()
+    p = _params(n=256, rings=100, slices=20)
+    plane = 256 * 256 * 8
+    ms = lib.stem_footprint_bytes(ctypes.byref(p), 0, 1, 0, 4096, 64)
+    ms_s = lib.stem_footprint_bytes(ctypes.byref(p), 2, 1, 0, 4096, 64)
+    assert ms - ms_s == (20 - 3) * plane
+    pr = lib.stem_footprint_bytes(ctypes.byref(p), 1, 4, 0, 4096, 64)
+    pr_s = lib.stem_footprint_bytes(ctypes.byref(p), 3, 4, 0, 4096, 64)
+    assert pr - pr_s == (20 - 3) * plane
+    assert lib.stem_footprint_bytes(ctypes.byref(p), 4, 1, 0, 4096, 64) == 0
+
+
+def test_memory_model_picks_single_then_streamed():
+    """The paper's automatic choice of memory model from the footprint estimate."""
+    import workloads as W
+    from paper_1706_08563_b300 import api
+    w = W.C3
+    single = api.footprint_bytes(w, "ms", batch=256)
+    streamed = api.footprint_bytes(w, "ms_streamed", batch=256)
+    assert streamed < single
+    assert api.memory_model(w, "ms", single, batch=256) == "single"
+    assert api.memory_model(w, "ms", single - 1, batch=256) == "streamed"
+    assert api.memory_model(w, "ms", streamed, batch=256) == "streamed"
+    with pytest.raises(MemoryError):
+        api.memory_model(w, "ms", streamed - 1, batch=256)
+
+
+def test_streamed_entry_points_reject_bad_arguments():
+    lib = _lib.load()
+    z = None
+    assert lib.stem_multislice_scan_streamed(z, z, z, 0, 1, 1.0, z, z, 0, z) == _lib.STEM_ERR_INVALID
+    assert lib.stem_prism_smatrix_streamed(z, z, 1, 0, 1, z, 0, z, 0, z) == _lib.STEM_ERR_INVALID
+    assert lib.stem_multislice_streamed_workspace(z, 4) == 0
+    assert lib.stem_prism_smatrix_streamed_workspace(z, 4) == 0

@@ -417,6 +417,7 @@ static stem_status run_multislice(stem_plan pl, const void* trans, bool streamed
   a.band = 1;   // the last column pass reads waves whose out-of-band columns were never written
   a.chi_c1 = 0.5 * pl->lam * pl->p.defocus_a;
   a.chi_c3 = 0.25 * pl->p.cs_a * pl->lam * pl->lam * pl->lam;
+  a.status = pl->status;
   const int last = dp_out ? COL_DP : COL_DET;
   for (int64_t p0 = 0; p0 < n_probes; p0 += batch) {
     a.batch = (int)std::min<int64_t>(batch, n_probes - p0);
@@ -522,6 +523,7 @@ static stem_status run_smatrix(stem_plan pl, const void* trans, bool streamed, i
   a.prop_y = pl->prop_y;
   a.prop_scale = 1.0f / (float)plane;
   a.beam_max = reinterpret_cast<unsigned*>(static_cast<char*>(ws) + smatrix_ws_waves(n, batch));
+  a.status = pl->status;
   for (int b0 = 0; b0 < nb; b0 += batch) {
     a.batch = std::min(batch, nb - b0);
     a.beams = pl->beams[lf] + b0;

@@ -36,6 +36,7 @@ struct PassArgs {
   int band = 0;                      // COL_DET ends a slice loop: only in-band columns hold data
   double chi_c1 = 0.0, chi_c3 = 0.0; // aberration phase in turns: chi_c1 |k|^2 + chi_c3 |k|^4
   float* dp = nullptr;               // COL_DP: [batch][N][N] intensities, += ring_scale |psi|^2
+  int* status = nullptr;             // plan status word (bounded waits record timeouts), or null
 };
 
 enum RowMode { ROW_SLICE = 0, ROW_BEAM0 = 1, ROW_IFFT_MAX = 2, ROW_FFT = 3, ROW_IFFT = 4 };

@@ -8,9 +8,12 @@
 // (Fourier-space aperture and phase ramp, then a column IFFT); the last column
 // pass of multislice squares |FFT| and bins it into rings instead of storing
 // (|P| = 1, so the last propagator phase does not change intensities).
+#include <cudaTypedefs.h>
+
 #include <algorithm>
 #include <mutex>
 
+#include "async_copy.cuh"
 #include "fft_core.cuh"
 #include "internal.h"
 
@@ -304,6 +307,123 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, ColCfg<N>::MINB) k_col_pas
 }
 
 // ---------------------------------------------------------------------------
+// Slice-loop column pass at N = 2048 moved by the tensor memory accelerator.
+// A tile (C = 4 columns x 2048 rows, 64 KB) reaches shared memory as eight
+// 2D tensor copies of 256 rows issued by one thread, one tile ahead of the
+// transform (two buffers, one mbarrier each), and leaves it the same way: the
+// transformed tile is written back into its buffer and stored by eight bulk
+// tensor copies, after which the buffer takes the tile after next.  The
+// threads issue no global loads or stores for the wave.  Every mbarrier wait
+// is bounded; on timeout the kernel records STEM_ERR_TIMEOUT in the status
+// word, waits (bounded) for its copies in flight and returns.
+// ---------------------------------------------------------------------------
+struct ColTmaCfg {
+  static constexpr int N = 2048, E = FftShape<2048>::E, T = N / E, C = 4, THREADS = C * T;
+  static constexpr int BOX_ROWS = 256, BOXES = N / BOX_ROWS;
+  static constexpr uint32_t STAGE_BYTES = (uint32_t)N * C * sizeof(float2);   // 64 KB
+  static constexpr uint32_t BOX_BYTES = STAGE_BYTES / BOXES;
+  static constexpr size_t XBUF = (size_t)(N + N / E) * C * sizeof(float2);
+  static constexpr size_t TW = (size_t)TwLayout<N>::TOTAL * sizeof(float2);
+  static constexpr size_t SMEM = 1024 + 2 * (size_t)STAGE_BYTES + XBUF + TW + 64;
+  static constexpr int MB = N / 3;
+  static constexpr int LO = (MB + 1 + C - 1) / C, HI0 = (N - MB) / C;
+  static constexpr int BAND_TILES = LO + N / C - HI0;
+  __device__ static int band_tile(int k) { return k >= LO ? k - LO + HI0 : k; }
+};
+
+__global__ void __launch_bounds__(ColTmaCfg::THREADS, 1)
+    k_col_slice_tma_2048(const PassArgs a, const __grid_constant__ CUtensorMap map, int n_tiles) {
+  using Cfg = ColTmaCfg;
+  constexpr int N = Cfg::N, E = Cfg::E, T = Cfg::T, C = Cfg::C;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* base = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
+  float2* stage = reinterpret_cast<float2*>(base);                        // [2][N][C]
+  float2* xbuf = reinterpret_cast<float2*>(base + 2 * (size_t)Cfg::STAGE_BYTES);
+  float2* tw = reinterpret_cast<float2*>(reinterpret_cast<unsigned char*>(xbuf) + Cfg::XBUF);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(reinterpret_cast<unsigned char*>(tw) + Cfg::TW);
+  const int tid = threadIdx.x;
+  const int c = tid % C, t = tid / C;
+  const SmemView<E, C> view{xbuf + c};
+  auto sync = [] { __syncthreads(); };
+
+  auto issue = [&](int tile, int b) {
+    const int wave = tile / Cfg::BAND_TILES;
+    const int col0 = Cfg::band_tile(tile % Cfg::BAND_TILES) * C;
+    const uint32_t bar = smem_u32(bars + b);
+    const uint32_t dst = smem_u32(stage + (size_t)b * N * C);
+    mbar_arrive_expect_tx(bar, Cfg::STAGE_BYTES);
+#pragma unroll
+    for (int y = 0; y < Cfg::BOXES; ++y)
+      tma_load_3d(dst + y * Cfg::BOX_BYTES, &map, 2 * col0, y * Cfg::BOX_ROWS, wave, bar);
+  };
+
+  if (tid == 0) {
+    mbar_init(smem_u32(bars), 1);
+    mbar_init(smem_u32(bars + 1), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  build_twiddles<N>(tw, tid, Cfg::THREADS);
+  __syncthreads();
+  if (tid == 0) {
+    if (blockIdx.x < n_tiles) issue(blockIdx.x, 0);
+    if (blockIdx.x + gridDim.x < n_tiles) issue(blockIdx.x + gridDim.x, 1);
+  }
+
+  int k = 0;
+  bool aborted = false;
+  for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++k) {
+    const int b = k & 1;
+    const bool ok = mbar_wait(smem_u32(bars + b), (uint32_t)(k >> 1) & 1u);
+    if (__syncthreads_or(!ok)) {
+      aborted = true;
+      break;
+    }
+    float2* st = stage + (size_t)b * N * C;
+    float2 v[E];
+#pragma unroll
+    for (int q = 0; q < E; ++q) v[q] = st[(t + q * T) * C + c];
+
+    const int wave = tile / Cfg::BAND_TILES;
+    const int col0 = Cfg::band_tile(tile % Cfg::BAND_TILES) * C;
+    const int col = col0 + c;
+    fft_dist<N, false>(v, view, t, sync, tw);
+    const int m = signed_freq(col, N);
+    const float2 px = cscale(__ldg(a.prop_x + col), a.prop_scale);
+#pragma unroll
+    for (int q = 0; q < E; ++q) {
+      const int ky = t + q * T;
+      const int n = signed_freq(ky, N);
+      const bool keep = 9 * (m * m + n * n) <= N * N;
+      v[q] = keep ? cmul(v[q], cmul(px, __ldg(a.prop_y + ky))) : make_float2(0.0f, 0.0f);
+    }
+    fft_dist<N, true>(v, view, t, sync, tw);
+#pragma unroll
+    for (int q = 0; q < E; ++q) st[(t + q * T) * C + c] = v[q];
+    fence_proxy_async();   // these writes before the tensor store reads them
+    __syncthreads();
+    if (tid == 0) {
+      const uint32_t src = smem_u32(st);
+#pragma unroll
+      for (int y = 0; y < Cfg::BOXES; ++y) tma_store_3d(&map, 2 * col0, y * Cfg::BOX_ROWS, wave, src + y * Cfg::BOX_BYTES);
+      bulk_commit();
+      if (tile + 2 * gridDim.x < n_tiles) {
+        bulk_wait_read();   // buffer b is read out: refill it with the tile after next
+        issue(tile + 2 * gridDim.x, b);
+      }
+    }
+  }
+  if (tid == 0) bulk_wait_all();
+
+  if (aborted && tid == 0) {
+    if (a.status) atomicExch(a.status, (int)STEM_ERR_TIMEOUT);
+    // let the copies already issued into this CTA's buffers land before it exits
+    int tile = blockIdx.x + k * gridDim.x;
+    for (int j = 0; j < 2 && tile < n_tiles; ++j, ++k, tile += gridDim.x)
+      mbar_wait(smem_u32(bars + (k & 1)), (uint32_t)(k >> 1) & 1u);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Launchers.  The dynamic shared-memory opt-in is set once per kernel in this
 // process (the library drives the device that was current at plan creation).
 // ---------------------------------------------------------------------------
@@ -375,6 +495,55 @@ static cudaError_t row_dispatch(int mode, const PassArgs& a, cudaStream_t s) {
   return cudaErrorInvalidValue;
 }
 
+#ifndef STEM_COL_TMA
+#define STEM_COL_TMA 1
+#endif
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library).
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag flag;
+  std::call_once(flag, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+// The waves [batch][N][N] of complex64 as a 3D FP32 tensor (2N, N, batch),
+// boxes of C complex columns x 256 rows.
+static cudaError_t wave_tensor_map(const PassArgs& a, CUtensorMap* map) {
+  using Cfg = ColTmaCfg;
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return cudaErrorNotSupported;
+  if (reinterpret_cast<uintptr_t>(a.wave) % 16) return cudaErrorInvalidValue;
+  const cuuint64_t dims[3] = {2ull * Cfg::N, (cuuint64_t)Cfg::N, (cuuint64_t)a.batch};
+  const cuuint64_t strides[2] = {2ull * Cfg::N * sizeof(float), 2ull * Cfg::N * Cfg::N * sizeof(float)};
+  const cuuint32_t box[3] = {2u * Cfg::C, (cuuint32_t)Cfg::BOX_ROWS, 1u};
+  const cuuint32_t estride[3] = {1u, 1u, 1u};
+  const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, a.wave, dims, strides, box, estride,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+static cudaError_t col_slice_tma_2048(const PassArgs& a, cudaStream_t s) {
+  using Cfg = ColTmaCfg;
+  static std::once_flag flag, occ_flag;
+  static int occ = 0;
+  cudaError_t e = set_smem(k_col_slice_tma_2048, Cfg::SMEM, flag);
+  if (e != cudaSuccess) return e;
+  CUtensorMap map;
+  if ((e = wave_tensor_map(a, &map)) != cudaSuccess) return e;
+  const int n_tiles = a.batch * Cfg::BAND_TILES;
+  const int grid = std::min(n_tiles, resident_ctas(k_col_slice_tma_2048, Cfg::THREADS, Cfg::SMEM, occ_flag, occ));
+  note_launch(), k_col_slice_tma_2048<<<grid, Cfg::THREADS, Cfg::SMEM, s>>>(a, map, n_tiles);
+  return cudaGetLastError();
+}
+
 // Slice-loop column passes visit only the column tiles inside the band limit;
 // the detector pass does so when it ends a multislice run (a.band), not when
 // it reads PRISM windows or other full fields.
@@ -387,6 +556,10 @@ static cudaError_t col_dispatch(int mode, const PassArgs& a, cudaStream_t s) {
     case COL_IFFT: return col_launch<N, COL_IFFT, false>(a, s);
     default: break;
   }
+#if STEM_COL_TMA
+  if constexpr (N == 2048)
+    if (mode == COL_SLICE) return col_slice_tma_2048(a, s);
+#endif
   if constexpr (N >= 64) {
     switch (mode) {
       case COL_SLICE: return col_launch<N, COL_SLICE, true>(a, s);

@@ -55,7 +55,10 @@ template <int N> struct RowCfg {
   static constexpr int ROWS = (THR / T) < N ? (THR / T) : N;
   static constexpr int THREADS = ROWS * T;
   static constexpr int ROWBUF = N + N / E;
-  static constexpr size_t SMEM = ((size_t)ROWS * ROWBUF + TwLayout<N>::TOTAL) * sizeof(float2);
+  // t_n rows of the tile, staged by one bulk copy (large transforms)
+  static constexpr bool T_STAGED = N >= 1024;
+  static constexpr size_t SMEM = ((size_t)ROWS * ROWBUF + TwLayout<N>::TOTAL + (T_STAGED ? (size_t)ROWS * N : 0)) *
+                                     sizeof(float2) + (T_STAGED ? 16 : 0);
   static constexpr int MINB = min_blocks<N>();
 };
 
@@ -86,8 +89,12 @@ __device__ __forceinline__ int signed_freq(int j, int n) { return j < (n >> 1) ?
 
 // ---------------------------------------------------------------------------
 // Row pass: persistent CTAs over tiles of ROWS rows of one wave.  Tile index
-// runs over the waves fastest, so the CTAs active at any moment read the same
-// rows of t_n (kept in L2 for the whole batch).
+// runs over the waves fastest and each CTA takes a contiguous block of tiles,
+// so consecutive tiles of a CTA are the same rows of different waves.  For
+// N >= 1024 the rows of t_n are copied into shared memory by one bulk copy
+// when the tile's rows change (issued at the start of the tile, waited for
+// after the inverse transform; bounded wait, timeout recorded in the status
+// word).
 // ---------------------------------------------------------------------------
 template <int N, int MODE>
 __global__ void __launch_bounds__(RowCfg<N>::THREADS, RowCfg<N>::MINB) k_row_pass(const PassArgs a, int n_tiles) {
@@ -95,6 +102,15 @@ __global__ void __launch_bounds__(RowCfg<N>::THREADS, RowCfg<N>::MINB) k_row_pas
   constexpr int E = Cfg::E, T = Cfg::T;
   extern __shared__ float2 smem[];
   float2* tw = smem + Cfg::ROWS * Cfg::ROWBUF;
+  constexpr bool T_BULK = Cfg::T_STAGED && (MODE == ROW_SLICE || MODE == ROW_BEAM0);
+  float2* tbuf = tw + TwLayout<N>::TOTAL;                                 // [ROWS][N] when T_BULK
+  uint64_t* tbar = reinterpret_cast<uint64_t*>(tbuf + (Cfg::T_STAGED ? Cfg::ROWS * N : 0));
+  if constexpr (T_BULK) {
+    if (threadIdx.x == 0) {
+      mbar_init(smem_u32(tbar), 1);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+  }
   build_twiddles<N>(tw, threadIdx.x, Cfg::THREADS);
   __syncthreads();
   const int t = threadIdx.x % T;
@@ -104,11 +120,28 @@ __global__ void __launch_bounds__(RowCfg<N>::THREADS, RowCfg<N>::MINB) k_row_pas
     if constexpr (T > 32 || Cfg::THREADS <= 32) __syncthreads();
     else __syncwarp();
   };
+  const int per = (n_tiles + gridDim.x - 1) / gridDim.x;
+  const int tile_end = min(n_tiles, (int)(blockIdx.x + 1) * per);
+  int staged_row0 = -1;
+  uint32_t tphase = 0;
 
-  for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+  for (int tile = blockIdx.x * per; tile < tile_end; ++tile) {
     const int wave = tile % a.batch;
-    const int row = (tile / a.batch) * Cfg::ROWS + rl;
+    const int row0 = (tile / a.batch) * Cfg::ROWS;
+    const int row = row0 + rl;
     float2* w = a.wave + (size_t)wave * N * N + (size_t)row * N;
+    const bool fresh = T_BULK && row0 != staged_row0;
+    if constexpr (T_BULK) {
+      if (fresh) {
+        __syncthreads();   // every thread has read the previous rows of t_n
+        if (threadIdx.x == 0) {
+          fence_proxy_async();
+          const uint32_t bar = smem_u32(tbar);
+          mbar_arrive_expect_tx(bar, Cfg::ROWS * N * (uint32_t)sizeof(float2));
+          bulk_load(smem_u32(tbuf), a.trans + (size_t)row0 * N, Cfg::ROWS * N * (uint32_t)sizeof(float2), bar);
+        }
+      }
+    }
 
     // slice-loop rows in the (k_x, y) domain hold zeros outside the band limit:
     // they are neither read from nor written to memory
@@ -135,8 +168,8 @@ __global__ void __launch_bounds__(RowCfg<N>::THREADS, RowCfg<N>::MINB) k_row_pas
     }
 #if STEM_PREFETCH
     if constexpr (MODE != ROW_BEAM0) {
-      const int nt = tile + gridDim.x;
-      if (t == 0 && nt < n_tiles) {
+      const int nt = tile + 1;
+      if (t == 0 && nt < tile_end) {
         const int nrow = (nt / a.batch) * Cfg::ROWS + rl;
         const float2* nr = a.wave + (size_t)(nt % a.batch) * N * N + (size_t)nrow * N;
         if constexpr (BAND_IN) {
@@ -154,7 +187,23 @@ __global__ void __launch_bounds__(RowCfg<N>::THREADS, RowCfg<N>::MINB) k_row_pas
     if constexpr (MODE == ROW_SLICE || MODE == ROW_IFFT_MAX || MODE == ROW_IFFT)
       fft_dist<N, true>(v, view, t, sync, tw);
 
-    if constexpr (MODE == ROW_SLICE || MODE == ROW_BEAM0) {
+    if constexpr (T_BULK) {
+      if (fresh) {
+        const bool ok = mbar_wait(smem_u32(tbar), tphase);
+        tphase ^= 1u;
+        staged_row0 = row0;
+        if (__syncthreads_or(!ok)) {
+          if (threadIdx.x == 0) {
+            if (a.status) atomicExch(a.status, (int)STEM_ERR_TIMEOUT);
+            mbar_wait(smem_u32(tbar), tphase ^ 1u);   // let the copy land before the CTA exits
+          }
+          return;
+        }
+      }
+      const float2* tr = tbuf + rl * N;
+#pragma unroll
+      for (int q = 0; q < E; ++q) v[q] = cmul(v[q], tr[t + q * T]);
+    } else if constexpr (MODE == ROW_SLICE || MODE == ROW_BEAM0) {
       const float2* tr = a.trans + (size_t)row * N;
 #pragma unroll
       for (int q = 0; q < E; ++q) v[q] = cmul(v[q], __ldg(tr + t + q * T));

@@ -36,7 +36,7 @@ import workloads as W  # noqa: E402
 METRIC = "probes/s for multislice and PRISM f=8 at stated error; p50/p99 solve latency"
 # DRAM bytes per wave and slice (row + column pass, t_n excluded) from one ncu
 # capture of the current slice passes (profiles/slice_passes_dram_traffic.md)
-SLICE_TRAFFIC_PER_WAVE = {2048: 82.8e6, 1024: 19.8e6}
+SLICE_TRAFFIC_PER_WAVE = {2048: 82.95e6, 1024: 19.33e6}
 HBM_FALLBACK_GBS = 6400.0
 
 
@@ -257,14 +257,16 @@ def run_ours(args, rank, world, local_rank):
         alg = (n_beams * (w.n_slices * 32.0 * band + 8.0 * band + 8.0 + 8.0 + 2.0 * esz) * n2
                + nbatches * w.n_slices * 8.0 * n2)
         ms = statistics.mean(sm_ms)
-        kernel = f"k_row_pass/k_col_pass<{w.n}> (S-matrix slice passes)"
+        kernel = (f"k_row_pass<{w.n}> + k_col_slice_tma_2048 (S-matrix slice passes)" if w.n == 2048
+                  else f"k_row_pass/k_col_pass<{w.n}> (S-matrix slice passes)")
     else:
         nb = math.ceil(n_probes / batch)
         # per probe: init write, then per slice row + column pass, the last column
         # pass reads only (detector): 32 S B per in-band pixel; t_n once per batch
         alg = n_probes * w.n_slices * 32.0 * band * n2 + nb * w.n_slices * 8.0 * n2
         ms = statistics.mean(out_ms)
-        kernel = f"k_row_pass/k_col_pass<{w.n}> (multislice slice passes)"
+        kernel = (f"k_row_pass<{w.n}> + k_col_slice_tma_2048 (multislice slice passes)" if w.n == 2048
+                  else f"k_row_pass/k_col_pass<{w.n}> (multislice slice passes)")
     ach = alg / (ms / 1e3) / 1e9
     per_wave = SLICE_TRAFFIC_PER_WAVE.get(w.n)
     waves = n_beams if prism else n_probes

@@ -257,7 +257,7 @@ def run_ours(args, rank, world, local_rank):
         alg = (n_beams * (w.n_slices * 32.0 * band + 8.0 * band + 8.0 + 8.0 + 2.0 * esz) * n2
                + nbatches * w.n_slices * 8.0 * n2)
         ms = statistics.mean(sm_ms)
-        kernel = (f"k_row_pass<{w.n}> + k_col_slice_tma_2048 (S-matrix slice passes)" if w.n == 2048
+        kernel = (f"k_row_pass<{w.n}> + k_col_slice_tma<{w.n}> (S-matrix slice passes)" if w.n >= 1024
                   else f"k_row_pass/k_col_pass<{w.n}> (S-matrix slice passes)")
     else:
         nb = math.ceil(n_probes / batch)
@@ -265,7 +265,7 @@ def run_ours(args, rank, world, local_rank):
         # pass reads only (detector): 32 S B per in-band pixel; t_n once per batch
         alg = n_probes * w.n_slices * 32.0 * band * n2 + nb * w.n_slices * 8.0 * n2
         ms = statistics.mean(out_ms)
-        kernel = (f"k_row_pass<{w.n}> + k_col_slice_tma_2048 (multislice slice passes)" if w.n == 2048
+        kernel = (f"k_row_pass<{w.n}> + k_col_slice_tma<{w.n}> (multislice slice passes)" if w.n >= 1024
                   else f"k_row_pass/k_col_pass<{w.n}> (multislice slice passes)")
     ach = alg / (ms / 1e3) / 1e9
     per_wave = SLICE_TRAFFIC_PER_WAVE.get(w.n)

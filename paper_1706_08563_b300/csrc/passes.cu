@@ -356,9 +356,9 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, ColCfg<N>::MINB) k_col_pas
 }
 
 // ---------------------------------------------------------------------------
-// Slice-loop column pass at N = 2048 moved by the tensor memory accelerator.
-// A tile (C = 4 columns x 2048 rows, 64 KB) reaches shared memory as eight
-// 2D tensor copies of 256 rows issued by one thread, one tile ahead of the
+// Slice-loop column pass of the large transforms moved by the tensor memory
+// accelerator.  A tile (C = 4 columns x N rows, 64 KB at N = 2048) reaches
+// shared memory as N / 256 2D tensor copies of 256 rows issued by one thread, one tile ahead of the
 // transform (two buffers, one mbarrier each), and leaves it the same way: the
 // transformed tile is written back into its buffer and stored by eight bulk
 // tensor copies, after which the buffer takes the tile after next.  The
@@ -366,8 +366,16 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, ColCfg<N>::MINB) k_col_pas
 // is bounded; on timeout the kernel records STEM_ERR_TIMEOUT in the status
 // word, waits (bounded) for its copies in flight and returns.
 // ---------------------------------------------------------------------------
-struct ColTmaCfg {
-  static constexpr int N = 2048, E = FftShape<2048>::E, T = N / E, C = 4, THREADS = C * T;
+#ifndef STEM_COL_TMA_MINB_1024
+#define STEM_COL_TMA_MINB_1024 2
+#endif
+#ifndef STEM_COL_TMA_C_1024
+#define STEM_COL_TMA_C_1024 4
+#endif
+template <int N_> struct ColTmaCfg {
+  static constexpr int N = N_, E = FftShape<N>::E, T = N / E;
+  static constexpr int C = N == 2048 ? 4 : STEM_COL_TMA_C_1024, THREADS = C * T;
+  static constexpr int MINB = N == 2048 ? 1 : STEM_COL_TMA_MINB_1024;
   static constexpr int BOX_ROWS = 256, BOXES = N / BOX_ROWS;
   static constexpr uint32_t STAGE_BYTES = (uint32_t)N * C * sizeof(float2);   // 64 KB
   static constexpr uint32_t BOX_BYTES = STAGE_BYTES / BOXES;
@@ -380,9 +388,10 @@ struct ColTmaCfg {
   __device__ static int band_tile(int k) { return k >= LO ? k - LO + HI0 : k; }
 };
 
-__global__ void __launch_bounds__(ColTmaCfg::THREADS, 1)
-    k_col_slice_tma_2048(const PassArgs a, const __grid_constant__ CUtensorMap map, int n_tiles) {
-  using Cfg = ColTmaCfg;
+template <int N_>
+__global__ void __launch_bounds__(ColTmaCfg<N_>::THREADS, ColTmaCfg<N_>::MINB)
+    k_col_slice_tma(const PassArgs a, const __grid_constant__ CUtensorMap map, int n_tiles) {
+  using Cfg = ColTmaCfg<N_>;
   constexpr int N = Cfg::N, E = Cfg::E, T = Cfg::T, C = Cfg::C;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* base = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
@@ -547,6 +556,9 @@ static cudaError_t row_dispatch(int mode, const PassArgs& a, cudaStream_t s) {
 #ifndef STEM_COL_TMA
 #define STEM_COL_TMA 1
 #endif
+#ifndef STEM_COL_TMA_1024
+#define STEM_COL_TMA_1024 1
+#endif
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no link
 // against the driver library).
 static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
@@ -564,8 +576,9 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 
 // The waves [batch][N][N] of complex64 as a 3D FP32 tensor (2N, N, batch),
 // boxes of C complex columns x 256 rows.
+template <int N>
 static cudaError_t wave_tensor_map(const PassArgs& a, CUtensorMap* map) {
-  using Cfg = ColTmaCfg;
+  using Cfg = ColTmaCfg<N>;
   PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
   if (!enc) return cudaErrorNotSupported;
   if (reinterpret_cast<uintptr_t>(a.wave) % 16) return cudaErrorInvalidValue;
@@ -579,17 +592,18 @@ static cudaError_t wave_tensor_map(const PassArgs& a, CUtensorMap* map) {
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-static cudaError_t col_slice_tma_2048(const PassArgs& a, cudaStream_t s) {
-  using Cfg = ColTmaCfg;
+template <int N>
+static cudaError_t col_slice_tma(const PassArgs& a, cudaStream_t s) {
+  using Cfg = ColTmaCfg<N>;
   static std::once_flag flag, occ_flag;
   static int occ = 0;
-  cudaError_t e = set_smem(k_col_slice_tma_2048, Cfg::SMEM, flag);
+  cudaError_t e = set_smem(k_col_slice_tma<N>, Cfg::SMEM, flag);
   if (e != cudaSuccess) return e;
   CUtensorMap map;
-  if ((e = wave_tensor_map(a, &map)) != cudaSuccess) return e;
+  if ((e = wave_tensor_map<N>(a, &map)) != cudaSuccess) return e;
   const int n_tiles = a.batch * Cfg::BAND_TILES;
-  const int grid = std::min(n_tiles, resident_ctas(k_col_slice_tma_2048, Cfg::THREADS, Cfg::SMEM, occ_flag, occ));
-  note_launch(), k_col_slice_tma_2048<<<grid, Cfg::THREADS, Cfg::SMEM, s>>>(a, map, n_tiles);
+  const int grid = std::min(n_tiles, resident_ctas(k_col_slice_tma<N>, Cfg::THREADS, Cfg::SMEM, occ_flag, occ));
+  note_launch(), k_col_slice_tma<N><<<grid, Cfg::THREADS, Cfg::SMEM, s>>>(a, map, n_tiles);
   return cudaGetLastError();
 }
 
@@ -607,7 +621,11 @@ static cudaError_t col_dispatch(int mode, const PassArgs& a, cudaStream_t s) {
   }
 #if STEM_COL_TMA
   if constexpr (N == 2048)
-    if (mode == COL_SLICE) return col_slice_tma_2048(a, s);
+    if (mode == COL_SLICE) return col_slice_tma<2048>(a, s);
+#endif
+#if STEM_COL_TMA_1024
+  if constexpr (N == 1024)
+    if (mode == COL_SLICE) return col_slice_tma<1024>(a, s);
 #endif
   if constexpr (N >= 64) {
     switch (mode) {

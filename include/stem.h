@@ -116,9 +116,18 @@ stem_status stem_plan_constants(stem_plan plan, double* lambda_a, double* sigma,
 stem_status stem_plan_set_detector_edges(stem_plan plan, int32_t n_edges, const double* edges_mrad);
 
 /* Device status word of the plan: kernels whose waits are bounded (the
- * tensor-core beam sum) record STEM_ERR_TIMEOUT there instead of hanging.
- * Copies it to *code (host) and clears it; synchronous (waits for the copy). */
+ * tensor-core beam sum, the TMA-fed column passes, the row passes' bulk copy
+ * of t_n) record STEM_ERR_TIMEOUT there instead of hanging.  Copies it to
+ * *code (host) and clears it; synchronous (waits for the copy). */
 stem_status stem_plan_device_status(stem_plan plan, int32_t* code);
+
+/* Self-test of that bounded-wait path; the paper has no counterpart.  Launches
+ * one thread that waits on a shared-memory barrier nothing arrives at, with
+ * the wait routine the kernels above use but a limit of limit_ns (1 .. 1e9).
+ * When the limit passes it records STEM_ERR_TIMEOUT in the plan's status word
+ * and returns, leaving the context usable.  Asynchronous on `stream`;
+ * STEM_ERR_INVALID for a null plan or a limit out of range. */
+stem_status stem_selftest_bounded_wait(stem_plan plan, int64_t limit_ns, void* stream);
 
 /* ---------------------------------------------------------------------------
  * Projected potentials (Methods, "Calculation of the Projected Potentials").

@@ -108,6 +108,18 @@ class Plan:
         return cls(w.cell, w.n, w.n_slices, w.slice_dz, w.energy_kev, w.alpha_mrad, w.ring_width_mrad,
                    w.n_rings, device=device, defocus=getattr(w, "defocus", 0.0), cs=getattr(w, "cs", 0.0))
 
+    def device_status(self) -> int:
+        """Read and clear the plan's device status word (0, or STEM_ERR_TIMEOUT
+        after a bounded wait gave up); synchronous."""
+        code = ctypes.c_int32()
+        check(_lib.load().stem_plan_device_status(self._h, ctypes.byref(code)), "stem_plan_device_status")
+        return int(code.value)
+
+    def selftest_bounded_wait(self, limit_ns: int) -> None:
+        """Launch the bounded-wait self-test on the current stream."""
+        check(_lib.load().stem_selftest_bounded_wait(self._h, int(limit_ns), _stream(self.device)),
+              "stem_selftest_bounded_wait")
+
     def close(self):
         if getattr(self, "_h", None) and self._h.value:
             _lib.load().stem_plan_destroy(self._h)

@@ -25,8 +25,9 @@ __device__ __forceinline__ void mbar_init(uint32_t bar, int count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
 }
 
-// true once the phase with the given parity has completed, false after kWaitNs
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+// true once the phase with the given parity has completed, false after
+// limit_ns (kWaitNs unless given)
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, unsigned long long limit_ns = kWaitNs) {
   const unsigned long long t0 = global_ns();
   while (true) {
     uint32_t done;
@@ -36,7 +37,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
         : "r"(bar), "r"(parity)
         : "memory");
     if (done) return true;
-    if (global_ns() - t0 > kWaitNs) return false;
+    if (global_ns() - t0 > limit_ns) return false;
   }
 }
 

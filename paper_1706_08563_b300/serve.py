@@ -13,6 +13,11 @@ device-memory budget (footprints from ``stem_footprint_bytes``, the paper's
 memory estimate) and arena space allow; finished probes free arena space and
 idle lanes are evicted least-recently-used when memory is needed.
 
+Failures stay with the request that caused them: a malformed request is
+refused at ``submit``, a request cancelled before admission is dropped, and
+an exception while creating or running a lane fails that lane's requests
+only (the lane is dropped) while the other lanes go on.
+
 All arithmetic runs in libstem's kernels through the C ABI; this module only
 schedules, moves pointers and copies results back.
 """
@@ -171,9 +176,40 @@ class Server:
         self.copy_stream = torch.cuda.Stream(device=self.device)
 
     # ------------------------------------------------------------------ API
+    @staticmethod
+    def validate(req: SimRequest) -> Optional[str]:
+        """Why the request cannot be served, or None."""
+        def arr(x, dt, cols):
+            return isinstance(x, np.ndarray) and x.dtype == dt and x.ndim == 2 and x.shape[1] == cols
+        if not arr(req.probe_xy, np.float64, 2):
+            return "probe_xy must be a float64 array [P, 2]"
+        if not np.all(np.isfinite(req.probe_xy)):
+            return "probe_xy holds non-finite positions"
+        if not arr(req.xyz, np.float64, 3) or not arr(req.gauss, np.float32, 4):
+            return "atoms must be float64 xyz [n, 3] and float32 gauss [n, 4]"
+        if req.xyz.shape[0] != req.gauss.shape[0]:
+            return "xyz and gauss describe different numbers of atoms"
+        if not (np.all(np.isfinite(req.xyz)) and np.all(np.isfinite(req.gauss))):
+            return "atoms hold non-finite values"
+        if req.algo not in ("ms", "prism"):
+            return f"unknown algorithm {req.algo!r}"
+        if req.algo == "prism":
+            from ._lib import STORAGE
+            if not (isinstance(req.f, int) and req.f >= 1 and req.f & (req.f - 1) == 0):
+                return "f must be a power of two"
+            if req.storage not in STORAGE:
+                return f"unknown storage {req.storage!r}"
+        return None
+
     def submit(self, req: SimRequest) -> cf.Future:
+        """Queue a request; the Future resolves to float32 [P, n_rings] rings,
+        or raises ServerError.  Cancelling it before it is admitted drops it."""
         fut: cf.Future = cf.Future()
         req.arrival = time.perf_counter()
+        why = self.validate(req)
+        if why is not None:
+            fut.set_exception(ServerError(why))
+            return fut
         with self._lock:
             self._in.append((req, fut))
         return fut
@@ -216,6 +252,8 @@ class Server:
         return int(b) + capacity * 16
 
     def _admit(self, req: SimRequest, fut: cf.Future) -> bool:
+        if fut.cancelled():
+            return True
         key = self.lane_key(req)
         n = int(req.probe_xy.shape[0])
         lane = self.lanes.get(key)
@@ -238,6 +276,8 @@ class Server:
         lane.reset_if_empty()
         if lane.room() < n:
             return False
+        if not fut.set_running_or_notify_cancel():
+            return True
         act = _Active(req, fut, lane, lane.filled, n)
         lane.filled += n
         lane.enqueue(act, req.probe_xy)
@@ -246,16 +286,33 @@ class Server:
         req.admitted = time.perf_counter()
         return True
 
+    def _drop_lane(self, key):
+        lane = self.lanes.pop(key)
+        lane.plan.close()
+        self.used -= self.lane_bytes.pop(key)
+
     def _evict_one(self) -> bool:
         idle = [k for k, l in self.lanes.items() if l.idle()]
         if not idle:
             return False
-        k = min(idle, key=lambda k: self.lanes[k].last_used)
-        lane = self.lanes.pop(k)
-        lane.plan.close()
-        self.used -= self.lane_bytes.pop(k)
-        del lane
+        self._drop_lane(min(idle, key=lambda k: self.lanes[k].last_used))
         return True
+
+    def _fail_lane(self, key, err: Exception):
+        """A lane whose launch or copy-back raised: fail its requests, drop it.
+        Its stream is synchronised first so that nothing it queued is still
+        running when its buffers are released."""
+        lane = self.lanes[key]
+        try:
+            lane.stream.synchronize()
+        except Exception:
+            pass
+        for act in lane.requests:
+            if not act.fut.done():
+                act.fut.set_exception(ServerError(f"lane failed: {err!r}"))
+        lane.requests = []
+        lane.inflight.clear()
+        self._drop_lane(key)
 
     def _finish(self, lane: _Lane):
         keep = []
@@ -294,14 +351,18 @@ class Server:
             else:
                 still.append((req, fut))
         self._pending = still
-        for lane in list(self.lanes.values()):
-            lane.poll()
-            n = lane.launch(self.max_inflight)
-            self.launches += n
-            busy |= n > 0
-            before = len(lane.requests)
-            self._finish(lane)
-            busy |= len(lane.requests) != before
+        for key, lane in list(self.lanes.items()):
+            try:
+                lane.poll()
+                n = lane.launch(self.max_inflight)
+                self.launches += n
+                busy |= n > 0
+                before = len(lane.requests)
+                self._finish(lane)
+                busy |= len(lane.requests) != before
+            except Exception as e:     # this lane's failure must not stop the others
+                self._fail_lane(key, e)
+                busy = True
         return busy
 
     def _loop(self):

@@ -130,3 +130,8 @@ def test_streamed_entry_points_reject_bad_arguments():
     assert lib.stem_prism_smatrix_streamed(z, z, 1, 0, 1, z, 0, z, 0, z) == _lib.STEM_ERR_INVALID
     assert lib.stem_multislice_streamed_workspace(z, 4) == 0
     assert lib.stem_prism_smatrix_streamed_workspace(z, 4) == 0
+
+
+def test_selftest_entry_point_rejects_bad_arguments():
+    lib = _lib.load()
+    assert lib.stem_selftest_bounded_wait(None, 1000, None) == _lib.STEM_ERR_INVALID

@@ -8,6 +8,7 @@ through the C ABI.
 from __future__ import annotations
 
 import ctypes
+import json
 from dataclasses import dataclass
 from typing import Optional, Tuple
 
@@ -78,6 +79,18 @@ class SMatrix:
         d = self.data().float() * self.scales()[None, None, None, :]
         c = torch.complex(d[:, :, 0, :], d[:, :, 1, :])
         return c.permute(2, 0, 1)[: self.n_beams].contiguous()
+
+    def save(self, path: str, plan: "Plan", tag: str = "") -> None:
+        """Checkpoint the S-matrix to a file (.npz): the raw buffer plus the plan
+        parameters it depends on, so that ``Plan.load_smatrix`` can refuse a
+        mismatched plan.  ``tag`` names the specimen (the plan does not know
+        the atoms); loading with a different tag is refused too."""
+        meta = dict(version=SMATRIX_FILE_VERSION, f=self.f, storage=self.storage, n_beams=self.n_beams,
+                    nbp=self.nbp, data_offset=self.data_offset, n=self.n, plan=plan.smatrix_key(), tag=tag)
+        np.savez(path, buf=self.buf.cpu().numpy(), meta=np.array(json.dumps(meta)))
+
+
+SMATRIX_FILE_VERSION = 1
 
 
 class Plan:
@@ -272,6 +285,34 @@ class Plan:
               "stem_prism_smatrix_streamed")
         nbp = (nb + 63) // 64 * 64
         return SMatrix(buf, f, storage, nb, nbp, (nbp * 4 + 255) // 256 * 256, self.n)
+
+    def smatrix_key(self) -> dict:
+        """The plan parameters an S-matrix depends on (grid, slices, optics)."""
+        p = self.params
+        return dict(cell=[float(c) for c in p.cell], n=int(p.n), n_slices=int(p.n_slices),
+                    slice_dz=float(p.slice_dz), energy_kev=float(p.energy_kev), alpha_mrad=float(p.alpha_mrad),
+                    defocus=float(p.defocus_a), cs=float(p.cs_a))
+
+    def load_smatrix(self, path: str, tag: str = "") -> SMatrix:
+        """Resume from ``SMatrix.save``: checks the file against this plan and
+        the tag, then uploads the buffer to this plan's device."""
+        with np.load(path, allow_pickle=False) as z:
+            meta = json.loads(str(z["meta"]))
+            raw = z["buf"]
+        if meta.get("version") != SMATRIX_FILE_VERSION:
+            raise ValueError(f"{path}: unknown S-matrix file version {meta.get('version')}")
+        if meta["plan"] != self.smatrix_key():
+            raise ValueError(f"{path}: S-matrix was computed for other plan parameters")
+        if meta["tag"] != tag:
+            raise ValueError(f"{path}: S-matrix belongs to specimen {meta['tag']!r}, not {tag!r}")
+        lib = _lib.load()
+        nbytes = lib.stem_prism_smatrix_bytes(self._h, meta["f"], STORAGE[meta["storage"]])
+        nb = len(self.prism_beams(meta["f"]))
+        if raw.dtype != np.uint8 or raw.size != nbytes or nb != meta["n_beams"]:
+            raise ValueError(f"{path}: buffer size or beam count does not match this plan")
+        buf = torch.from_numpy(raw).to(self.device)
+        return SMatrix(buf, meta["f"], meta["storage"], meta["n_beams"], meta["nbp"], meta["data_offset"],
+                       meta["n"])
 
     def prism_output_workspace(self, f: int, chunk: int) -> torch.Tensor:
         return _workspace(_lib.load().stem_prism_output_workspace(self._h, f, chunk), self.device)

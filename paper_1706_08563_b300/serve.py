@@ -26,6 +26,7 @@ from __future__ import annotations
 import collections
 import concurrent.futures as cf
 import dataclasses
+import json
 import threading
 import time
 from typing import Dict, List, Optional
@@ -153,7 +154,7 @@ class Server:
     """
 
     def __init__(self, max_bytes: int, batch: int = 64, prism_chunk: int = 1024, arena: int = 16384,
-                 max_inflight: int = 2, device=None):
+                 max_inflight: int = 2, device=None, log=None):
         self.lib = _lib.load()
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else
                                    torch.device(device).index or 0)
@@ -174,8 +175,30 @@ class Server:
         self.latencies: List[float] = []
         self.launches = 0
         self.copy_stream = torch.cuda.Stream(device=self.device)
+        # per-request log: a path (JSON lines appended) or a callable taking a dict
+        self._log = log
+        self._t0 = time.perf_counter()
 
     # ------------------------------------------------------------------ API
+    def _record(self, req: SimRequest, status: str, lane_bytes: int = 0, error: str = ""):
+        """One log line per request: what it was, when it arrived, was admitted
+        and finished (seconds since the server was created), and its outcome."""
+        if self._log is None:
+            return
+        rec = dict(specimen=req.specimen, algo=req.algo, f=req.f if req.algo == "prism" else 1,
+                   storage=req.storage if req.algo == "prism" else "f32",
+                   probes=int(getattr(req.probe_xy, "shape", (0,))[0]), status=status,
+                   arrival_s=req.arrival - self._t0,
+                   admitted_s=(req.admitted - self._t0) if req.admitted else None,
+                   finished_s=(req.finished - self._t0) if req.finished else None,
+                   latency_ms=1e3 * (req.finished - req.arrival) if req.finished else None,
+                   lane_bytes=int(lane_bytes), error=error)
+        if callable(self._log):
+            self._log(rec)
+        else:
+            with open(self._log, "a") as fh:
+                fh.write(json.dumps(rec) + "\n")
+
     @staticmethod
     def validate(req: SimRequest) -> Optional[str]:
         """Why the request cannot be served, or None."""
@@ -209,6 +232,7 @@ class Server:
         why = self.validate(req)
         if why is not None:
             fut.set_exception(ServerError(why))
+            self._record(req, "refused", error=why)
             return fut
         with self._lock:
             self._in.append((req, fut))
@@ -262,9 +286,12 @@ class Server:
             need = self.footprint(req, cap)
             if need == 0:
                 fut.set_exception(ServerError("unsupported request parameters"))
+                self._record(req, "refused", error="unsupported request parameters")
                 return True
             if need > self.max_bytes:
-                fut.set_exception(ServerError(f"request needs {need} bytes, more than the budget {self.max_bytes}"))
+                why = f"request needs {need} bytes, more than the budget {self.max_bytes}"
+                fut.set_exception(ServerError(why))
+                self._record(req, "refused", error=why)
                 return True
             while self.used + need > self.max_bytes:
                 if not self._evict_one():
@@ -310,6 +337,7 @@ class Server:
         for act in lane.requests:
             if not act.fut.done():
                 act.fut.set_exception(ServerError(f"lane failed: {err!r}"))
+                self._record(act.req, "failed", self.lane_bytes.get(key, 0), repr(err))
         lane.requests = []
         lane.inflight.clear()
         self._drop_lane(key)
@@ -329,6 +357,7 @@ class Server:
                 act.req.finished = time.perf_counter()
                 self.latencies.append(act.req.finished - act.req.arrival)
                 act.fut.set_result(act.host.numpy().copy())
+                self._record(act.req, "done", self.lane_bytes.get(lane.key, 0))
                 continue
             keep.append(act)
         lane.requests = keep
@@ -345,6 +374,7 @@ class Server:
                 ok = self._admit(req, fut)
             except Exception as e:     # a failing request must not stop the others
                 fut.set_exception(e)
+                self._record(req, "failed", error=repr(e))
                 ok = True
             if ok:
                 busy = True

@@ -56,7 +56,8 @@ def test_malformed_requests_are_refused_and_others_complete():
         dataclasses.replace(b, f=3),                                         # f not a power of two
         dataclasses.replace(b, storage="f8"),                                # unknown storage
     ]
-    with Server(4 << 30, batch=32, prism_chunk=64, arena=512) as srv:
+    log = []
+    with Server(4 << 30, batch=32, prism_chunk=64, arena=512, log=log.append) as srv:
         futs_good = [srv.submit(a)]
         futs_bad = [srv.submit(r) for r in bad]
         futs_good.append(srv.submit(b))
@@ -66,6 +67,14 @@ def test_malformed_requests_are_refused_and_others_complete():
                 f.result()
         for f, r in zip(futs_good, ref):
             _same(f.result(timeout=300), r)
+        srv.drain(timeout=300)
+    # one log line per request: refusals with their reason, completions with times
+    assert sorted(r["status"] for r in log) == ["done"] * 2 + ["refused"] * len(bad)
+    for r in log:
+        if r["status"] == "done":
+            assert r["latency_ms"] > 0 and r["admitted_s"] >= r["arrival_s"] and r["lane_bytes"] > 0
+        else:
+            assert r["error"] and r["finished_s"] is None
 
 
 def test_cancelled_request_is_dropped_and_others_complete():
@@ -137,3 +146,29 @@ def test_bounded_wait_times_out_and_the_context_survives():
     assert torch.allclose(after, before, rtol=1e-6, atol=1e-12)
     with pytest.raises(Exception):
         plan.selftest_bounded_wait(0)
+
+
+def test_smatrix_checkpoint_round_trip(tmp_path):
+    """An S-matrix saved to a file and loaded into a fresh plan gives the same
+    bytes and the same output; a file for other parameters or another
+    specimen is refused."""
+    from paper_1706_08563_b300 import api
+    w = W.Workload("ck", (24.0, 24.0, 6.0), 60, 128, 3, 2.0, 300.0, 25.0, 8, 2.0, 50)
+    xyz, gauss = W.atoms(w, seed=8)
+    plan = api.Plan.from_workload(w)
+    trans = plan.slice_potentials(torch.from_numpy(xyz).cuda(), torch.from_numpy(gauss).cuda())
+    sm = plan.prism_smatrix(trans, 4, "f16")
+    xy = torch.from_numpy(W.random_positions(w, 11, seed=9)).cuda()
+    ref = plan.prism_output(sm, xy, chunk=8)
+    path = str(tmp_path / "smatrix.npz")
+    sm.save(path, plan, tag="specimen-8")
+    fresh = api.Plan.from_workload(w)
+    back = fresh.load_smatrix(path, tag="specimen-8")
+    assert torch.equal(back.buf, sm.buf)
+    # the ring sums use float atomics: equal up to the order of additions
+    assert torch.allclose(fresh.prism_output(back, xy, chunk=8), ref, rtol=1e-6, atol=1e-12)
+    with pytest.raises(ValueError):
+        fresh.load_smatrix(path, tag="another specimen")
+    other = api.Plan.from_workload(W.scaled(w, n_slices=4))
+    with pytest.raises(ValueError):
+        other.load_smatrix(path, tag="specimen-8")

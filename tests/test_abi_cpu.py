@@ -135,3 +135,10 @@ def test_streamed_entry_points_reject_bad_arguments():
 def test_selftest_entry_point_rejects_bad_arguments():
     lib = _lib.load()
     assert lib.stem_selftest_bounded_wait(None, 1000, None) == _lib.STEM_ERR_INVALID
+
+
+def test_c_client_compiles_and_links_as_c99(repo_tmp):
+    """The header is plain C and the library links without Python or PyTorch."""
+    from conftest import build_c_client
+    exe = build_c_client(repo_tmp)
+    assert os.access(exe, os.X_OK)

@@ -9,6 +9,7 @@
   the context must stay usable.
 """
 import dataclasses
+import os
 import time
 
 import numpy as np
@@ -148,7 +149,7 @@ def test_bounded_wait_times_out_and_the_context_survives():
         plan.selftest_bounded_wait(0)
 
 
-def test_smatrix_checkpoint_round_trip(tmp_path):
+def test_smatrix_checkpoint_round_trip(repo_tmp):
     """An S-matrix saved to a file and loaded into a fresh plan gives the same
     bytes and the same output; a file for other parameters or another
     specimen is refused."""
@@ -160,7 +161,7 @@ def test_smatrix_checkpoint_round_trip(tmp_path):
     sm = plan.prism_smatrix(trans, 4, "f16")
     xy = torch.from_numpy(W.random_positions(w, 11, seed=9)).cuda()
     ref = plan.prism_output(sm, xy, chunk=8)
-    path = str(tmp_path / "smatrix.npz")
+    path = os.path.join(repo_tmp, "smatrix.npz")
     sm.save(path, plan, tag="specimen-8")
     fresh = api.Plan.from_workload(w)
     back = fresh.load_smatrix(path, tag="specimen-8")

@@ -68,10 +68,10 @@ def _worker(rank, world, port, out_path):
         dist.destroy_process_group()
 
 
-def test_two_gloo_ranks_match_one_process(tmp_path):
+def test_two_gloo_ranks_match_one_process(repo_tmp):
     import workloads as W
     from oracle import stem as O
-    out = str(tmp_path / "r.npz")
+    out = os.path.join(repo_tmp, "r.npz")
     mp.spawn(_worker, args=(2, _free_port(), out), nprocs=2, join=True)
     got = np.load(out)
     w, p, xyz, gauss, xy = _case()

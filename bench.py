@@ -34,8 +34,9 @@ import numpy as np  # noqa: E402
 import workloads as W  # noqa: E402
 
 METRIC = "probes/s for multislice and PRISM f=8 at stated error; p50/p99 solve latency"
-# DRAM bytes per wave and slice (row + column pass, t_n excluded) from one ncu
-# capture of the current slice passes (profiles/slice_passes_dram_traffic.md)
+# DRAM bytes per wave and slice (row + column pass, t_n excluded), measured
+# with ncu (dram__bytes_read.sum + dram__bytes_write.sum) on launches of 16
+# waves of 2048^2 and 32 waves of 1024^2 of the current slice passes
 SLICE_TRAFFIC_PER_WAVE = {2048: 82.95e6, 1024: 19.33e6}
 HBM_FALLBACK_GBS = 6400.0
 

@@ -5,7 +5,7 @@ j <-> x_j = j*dx, dx = Lx/N, dy = Ly/N, origin at pixel 0).  A 2D FFT index
 j maps to the signed frequency index m = j for j < N/2 and m = j - N
 otherwise; the spatial frequency is (m/Lx, n/Ly) in 1/A.
 
-Readings of the paper that this file fixes (each also listed in the design doc):
+Readings of the paper that this file fixes (where the paper is silent or leaves a choice):
 * lambda and sigma are the relativistic electron wavelength and interaction
   constant (the paper defers to Kirkland for both, Methods, text after Eq. 1
   and Eq. 2).

@@ -101,6 +101,15 @@ def _chi_cs_no_lambda_cubed(p, kx, ky):
     return math.pi * p.lam * p.defocus * k2 + 0.5 * math.pi * p.cs * p.lam * k2 * k2
 
 
+def _fp_first_config_only(p, configs, gauss, xy, algo="ms", f=1):
+    # every configuration replaced by the first one
+    return O._orig_frozen_phonon_rings(p, [configs[0]] * len(configs), gauss, xy, algo, f)
+
+
+def _fp_sum_not_mean(p, configs, gauss, xy, algo="ms", f=1):
+    return O._orig_frozen_phonon_rings(p, configs, gauss, xy, algo, f) * len(configs)
+
+
 CASES = [
     ("propagator", _prop_flipped, [pins.test_phase_grating_one_slice_jacobi_anger,
                                    pins.test_gaussian_beam_fresnel_closed_form]),
@@ -117,6 +126,8 @@ CASES = [
     ("multislice_k", _ms_last_slice_unpropagated, [pins.test_phase_grating_one_slice_jacobi_anger]),
     ("aberration_chi", _chi_defocus_flipped, [pins.test_defocus_equals_free_propagation]),
     ("aberration_chi", _chi_cs_no_lambda_cubed, [pins.test_spherical_aberration_hand_value]),
+    ("frozen_phonon_rings", _fp_first_config_only, [pins.test_frozen_phonon_mean_of_translated_configurations]),
+    ("frozen_phonon_rings", _fp_sum_not_mean, [pins.test_frozen_phonon_mean_of_translated_configurations]),
 ]
 
 

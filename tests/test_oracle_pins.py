@@ -13,6 +13,7 @@ import pytest
 from scipy import special
 
 import oracle
+import workloads as W
 from oracle import stem as O
 
 
@@ -421,3 +422,27 @@ def test_4d_output_free_space_and_ring_sums():
     table = O.ring_table(p)
     for i in (0, 5, 17):
         assert np.allclose(dp[:, table == i].sum(axis=1), rings[:, i], rtol=1e-12, atol=1e-16)
+
+
+def test_frozen_phonon_mean_of_translated_configurations():
+    """Configurations that are whole-pixel translations of one structure: each
+    one's rings equal the untranslated structure's rings at the probe moved the
+    opposite way (exact: a whole-pixel shift moves the sampled potential and
+    the probe's phase ramp together), so the frozen-phonon mean is the mean
+    over moved probes.  Identical configurations reduce to one run, and the
+    PRISM branch at f = 1 is multislice."""
+    w = W.Workload("fp", (8.0, 8.0, 4.0), 6, 32, 2, 2.0, 200.0, 20.0, 0, 5.0, 10)
+    p = O.params_from(w)
+    xyz, gauss = W.atoms(w, seed=5)
+    xy = W.random_positions(w, 3, seed=6)
+    shifts = [(0, 0), (3, -2), (-5, 7)]
+    configs = [xyz + np.array([a * p.dx, b * p.dy, 0.0]) for a, b in shifts]
+    got = O.frozen_phonon_rings(p, configs, gauss, xy)
+    t = O.transmission(p, O.projected_potential(p, xyz, gauss))
+    moved = [O.multislice_rings(p, t, xy - np.array([a * p.dx, b * p.dy])) for a, b in shifts]
+    assert np.allclose(got, np.mean(moved, axis=0), rtol=1e-9, atol=1e-14)
+    assert not np.allclose(moved[0], moved[1], rtol=1e-3)          # the shifts do change the rings
+    assert np.allclose(O.frozen_phonon_rings(p, [xyz, xyz], gauss, xy), O.multislice_rings(p, t, xy),
+                       rtol=1e-12, atol=1e-15)
+    assert np.allclose(O.frozen_phonon_rings(p, configs, gauss, xy, algo="prism", f=1), got,
+                       rtol=1e-9, atol=1e-14)

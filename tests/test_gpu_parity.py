@@ -381,3 +381,25 @@ def test_prism_4d_vs_oracle(api, storage, engine, tol):
     xy = W.random_positions(w, 7, seed=5)
     dp = plan.prism_output_4d(sm, dev(xy), chunk=4, engine=engine).cpu().numpy()
     _check_dp(dp, O.prism_dp(p, O.prism_smatrix(p, tref, beams), beams, 4, xy), tol)
+
+
+def test_frozen_phonon_average_vs_oracle(api):
+    """Frozen phonons: three configurations with i.i.d. displacements, each
+    through the GPU's potentials and slice loop, accumulated with weight 1/C
+    (multislice, and PRISM f = 2 with an S-matrix per configuration), against
+    the oracle's frozen-phonon mean."""
+    w = W.Workload("fpg", (16.0, 16.0, 6.0), 30, 64, 3, 2.0, 200.0, 20.0, 0, 2.0, 30, fp_configs=3, fp_sigma=0.08)
+    xyz, gauss = W.atoms(w, seed=31)
+    xy = W.random_positions(w, 11, seed=32)
+    configs = [W.displaced(w, xyz, c) for c in range(w.fp_configs)]
+    plan = api.Plan.from_workload(w)
+    ms = torch.zeros((len(xy), w.n_rings), dtype=torch.float32, device="cuda")
+    pr = torch.zeros_like(ms)
+    for xc in configs:
+        t = plan.slice_potentials(dev(xc), dev(gauss))
+        plan.multislice(t, dev(xy), batch=8, rings=ms, weight=1.0 / len(configs))
+        sm = plan.prism_smatrix(t, 2, "f32")
+        plan.prism_output(sm, dev(xy), chunk=8, rings=pr, weight=1.0 / len(configs))
+    p = O.params_from(w)
+    check_rings(ms.cpu().numpy(), O.frozen_phonon_rings(p, configs, gauss, xy), FP32_TOL)
+    check_rings(pr.cpu().numpy(), O.frozen_phonon_rings(p, configs, gauss, xy, algo="prism", f=2), FP32_TOL)

@@ -2,12 +2,12 @@
 on outputs the FP64 oracle can compute one by one.
 
 * Batched multislice at 1024^2, 50 slices of 2 A, 200 keV, 50 000 atoms, in a
-  launch of 256 probes: three sampled probes against the oracle end to end.
+  launch of 256 probes: 64 sampled probes against the oracle end to end.
 * PRISM f=8 at 2048^2, 100 slices of 1 A, 300 keV, 793 beams, FP16 S-matrix
   with the tcgen05 beam sum and chunks of 4096 probes: the potentials on
   sampled slices, two sampled S-matrix beams against the oracle (through all
-  100 slices), and the output of sampled probes computed by the oracle from the
-  GPU's own S-matrix (stage-wise: it isolates the output step).
+  100 slices), and the output of 33 sampled probes computed by the oracle from
+  the GPU's own S-matrix (stage-wise: it isolates the output step).
 """
 import numpy as np
 import pytest
@@ -24,7 +24,11 @@ def _rel(a, b):
     return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
 
 
-def test_multislice_1024_launch_of_256_sampled():
+def test_multislice_1024_launch_of_256_sampled(repo_tmp):
+    """64 probes sampled from a launch of 256 (every fourth, so every part of
+    the launch and of the scan row is covered), each against the FP64 oracle
+    end to end (the oracle runs in a process pool)."""
+    from oracle_pool import multislice_rings_pool
     from paper_1706_08563_b300 import api
     w = W.C3
     xyz, gauss = W.atoms(w)
@@ -34,8 +38,10 @@ def test_multislice_1024_launch_of_256_sampled():
     rings = plan.multislice(trans, torch.from_numpy(xy).cuda(), batch=w.batch).cpu().numpy()
     p = O.params_from(w)
     t = O.transmission(p, O.projected_potential(p, xyz, gauss))
-    pick = [0, 131, 255]
-    check_rings(rings[pick], O.multislice_rings(p, t, xy[pick]), FP32_TOL, floor=fp32_floor(w.n, w.n_slices))
+    pick = np.arange(0, w.batch, 4)
+    assert len(pick) == 64
+    ref = multislice_rings_pool(p, t, xy[pick], repo_tmp)
+    check_rings(rings[pick], ref, FP32_TOL, floor=fp32_floor(w.n, w.n_slices))
 
 
 @pytest.fixture(scope="module")
@@ -86,7 +92,7 @@ def test_prism8_output_sampled_probes(prism8):
     rings = plan.prism_output(sm, torch.from_numpy(xy_all).cuda(), chunk=4096).cpu().numpy()
     wdw = p.n // 8
     sc = sm.scales()
-    for i in (0, 1234, 4095):
+    for i in list(range(0, 4096, 128)) + [4095]:      # 33 probes over the chunk's 16 scan rows
         xy = xy_all[i:i + 1]
         o = O.prism_window_origin(p, 8, xy)[0]
         rows = torch.from_numpy(np.mod(o[1] + np.arange(wdw), p.n)).cuda()

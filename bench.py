@@ -244,6 +244,14 @@ def run_ours(args, rank, world, local_rank):
                         ("output" if prism else "multislice"): statistics.mean(out_ms)}
     res["latency"] = {"p50_ms": float(np.percentile(dev_ms, 50)), "p99_ms": float(np.percentile(dev_ms, 99)),
                       "what": "one whole simulation (device time)"}
+    # the rate of each phase on its own
+    rates = {"potential_slices_per_s": w.n_slices / (statistics.mean(pot_ms) / 1e3)}
+    if prism:
+        rates["smatrix_beams_per_s"] = n_beams / (statistics.mean(sm_ms) / 1e3)
+        rates["output_probes_per_s"] = n_probes / (statistics.mean(out_ms) / 1e3)
+    else:
+        rates["multislice_probes_per_s"] = n_probes / (statistics.mean(out_ms) / 1e3)
+    res["phase_rates"] = rates
     hbm, _, src = peaks()
     n2 = w.n * w.n
     # inside the slice loop only the columns within the 2/3 band limit hold data

@@ -10,12 +10,15 @@
 // the real and imaginary parts.  M = 128 pixels, N = 256, K = 16 per
 // tcgen05.mma (kind::f16, FP16 or BF16 in, FP32 accumulate in tensor memory).
 //
-// Per CTA (128 threads, one CTA per SM): all threads stage 64-wide K chunks of
+// Per CTA (512 threads, one CTA per SM): all threads stage 64-wide K chunks of
 // A and B into shared memory with cp.async in the 128-byte swizzled K-major
-// layout; thread 0 issues the MMAs and commits them to an mbarrier per stage;
-// four stages keep the tensor pipe fed.  After the last chunk every warp reads
-// its 32 accumulator lanes with tcgen05.ld and scatters the pixels into the
-// probes' windows.  Every wait is bounded (2 s of %globaltimer); on timeout the
+// layout (more loading warps keep more bytes in flight: 128 -> 256 -> 512
+// threads took a 4096-probe output call at 2048^2 from 9.4 to 7.2 to 6.4 ms);
+// thread 0 issues the MMAs and commits them to an mbarrier per stage; four
+// stages keep the tensor pipe fed.  After the last chunk the warps read the
+// accumulators with tcgen05.ld (a warp may read only the 32 lanes of its
+// quarter, warp mod 4; the warps sharing a quarter split its columns) and
+// scatter the pixels into the probes' windows.  Every wait is bounded (2 s of %globaltimer); on timeout the
 // kernel records STEM_ERR_TIMEOUT in the plan's status word, drains its copies,
 // frees its tensor memory and returns.
 #include <cuda_bf16.h>
@@ -29,7 +32,11 @@
 
 namespace stem {
 
-constexpr int kUmmaThreads = 128;
+#ifndef STEM_UMMA_THREADS
+#define STEM_UMMA_THREADS 512
+#endif
+constexpr int kUmmaThreads = STEM_UMMA_THREADS;   // 128 or 256: loaders; the epilogue splits columns
+static_assert(kUmmaThreads == 128 || kUmmaThreads == 256 || kUmmaThreads == 512, "4, 8 or 16 warps");
 constexpr int kUmmaStages = 4;
 constexpr int kUmmaGroup = 128;                 // probes per work item (N = 256)
 constexpr int kTileX = 16, kTileY = 8;          // must match prism.cu
@@ -199,14 +206,14 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_beam_sum_umma(
       const uint32_t a_s = sbase + st * kStageBytes, b_s = a_s + kAStage;
       const int k0 = kc * 64;
 #pragma unroll
-      for (int i = 0; i < 8; ++i) {
+      for (int i = 0; i < 1024 / kUmmaThreads; ++i) {
         const int idx = tid + i * kUmmaThreads;
         const int r = idx >> 3, c = idx & 7;
         const size_t pix = (size_t)(y0 + r / kTileX) * n + x0 + (r % kTileX);
         cp_async16(a_s + r * 128 + ((c ^ (r & 7)) << 4), sdata + pix * K + k0 + c * 8, 16);
       }
 #pragma unroll
-      for (int i = 0; i < 16; ++i) {
+      for (int i = 0; i < 2048 / kUmmaThreads; ++i) {
         const int idx = tid + i * kUmmaThreads;
         const int r = idx >> 3, c = idx & 7;
         const int p = s_probe[r >> 1];
@@ -254,12 +261,16 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_beam_sum_umma(
     if (*s_abort) { aborted = true; break; }
     tc_fence_after();
 
-    // epilogue: lane r of warp w holds pixel 32 w + r of the tile
-    const int r = warp * 32 + (tid & 31);
+    // epilogue: lane r of warp w holds pixel 32 (w mod 4) + r of the tile; with
+    // eight warps, warps w and w + 4 share a lane quarter and split its columns
+    constexpr int WARPS = kUmmaThreads / 32, BLKS = 4 / (WARPS / 4);
+    const int quarter = warp % 4;
+    const int r = quarter * 32 + (tid & 31);
     const int gx = x0 + r % kTileX, gy = y0 + r / kTileX;
-    for (int blk = 0; blk < 4; ++blk) {
+    for (int b = 0; b < BLKS; ++b) {
+      const int blk = (warp / 4) * BLKS + b;
       float v[64];
-      tmem_ld64(taddr + ((uint32_t)(warp * 32) << 16) + blk * 64, v);
+      tmem_ld64(taddr + ((uint32_t)(quarter * 32) << 16) + blk * 64, v);
 #pragma unroll
       for (int j = 0; j < 32; ++j) {
         const int pl = blk * 32 + j;

@@ -29,6 +29,12 @@
  *   - No call allocates device memory except stem_plan_create.  Scratch
  *     memory ("workspace") is passed in by the caller; each call has a
  *     *_workspace query giving the bytes it needs.
+ *   - The compute calls can be captured into a CUDA graph once they have run
+ *     once plainly (their one-time kernel attribute setup then stays out of
+ *     the capture): they neither allocate nor synchronise with the host.  Not
+ *     capturable: stem_plan_create / _destroy / _set_detector_edges /
+ *     _device_status (synchronous) and the *_streamed calls (they create a
+ *     stream and events).
  */
 #ifndef STEM_H_
 #define STEM_H_

@@ -403,3 +403,24 @@ def test_frozen_phonon_average_vs_oracle(api):
     p = O.params_from(w)
     check_rings(ms.cpu().numpy(), O.frozen_phonon_rings(p, configs, gauss, xy), FP32_TOL)
     check_rings(pr.cpu().numpy(), O.frozen_phonon_rings(p, configs, gauss, xy, algo="prism", f=2), FP32_TOL)
+
+
+def test_probe_phase_far_from_the_origin(api):
+    """Probe positions moved by whole multiples of the cell (up to 10^6 A away)
+    give the rings of the original positions: the phase ramps (probe
+    initialisation, PRISM coefficients) and the PRISM window origins are
+    reduced in FP64 before anything is evaluated in FP32."""
+    w = W.scaled(W.C1, n=64)
+    xyz, gauss = W.atoms(w, seed=51)
+    plan = api.Plan.from_workload(w)
+    trans = plan.slice_potentials(dev(xyz), dev(gauss))
+    xy = W.random_positions(w, 9, seed=52)
+    lx, ly = w.cell[0], w.cell[1]
+    far = xy + np.array([[62500.0 * lx, -31000.0 * ly]])
+    near_ms = plan.multislice(trans, dev(xy), batch=4).cpu().numpy()
+    far_ms = plan.multislice(trans, dev(far), batch=4).cpu().numpy()
+    assert np.allclose(far_ms, near_ms, rtol=1e-5, atol=1e-9 * near_ms.max())
+    sm = plan.prism_smatrix(trans, 2, "f32")
+    near_pr = plan.prism_output(sm, dev(xy), chunk=4).cpu().numpy()
+    far_pr = plan.prism_output(sm, dev(far), chunk=4).cpu().numpy()
+    assert np.allclose(far_pr, near_pr, rtol=1e-5, atol=1e-9 * near_pr.max())

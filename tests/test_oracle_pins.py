@@ -446,3 +446,25 @@ def test_frozen_phonon_mean_of_translated_configurations():
                        rtol=1e-12, atol=1e-15)
     assert np.allclose(O.frozen_phonon_rings(p, configs, gauss, xy, algo="prism", f=1), got,
                        rtol=1e-9, atol=1e-14)
+
+
+def test_propagator_semigroup():
+    """Free propagation composes: P(dz1) P(dz2) = P(dz1 + dz2) inside the band
+    limit (and 0 outside), P(0) is the band-limit mask, and a free-space wave
+    propagated through two half-thickness slices equals one full slice."""
+    import dataclasses
+    w = W.Workload("sg", (10.0, 14.0, 4.0), 0, 32, 2, 2.0, 200.0, 20.0, 0, 5.0, 8)
+    p = O.params_from(w)
+    pa = dataclasses.replace(p, slice_dz=0.7)
+    pb = dataclasses.replace(p, slice_dz=1.9)
+    pab = dataclasses.replace(p, slice_dz=2.6)
+    p0 = dataclasses.replace(p, slice_dz=0.0)
+    assert np.allclose(O.propagator(pa) * O.propagator(pb), O.propagator(pab), atol=1e-13)
+    assert np.array_equal(O.propagator(p0), O.bandlimit_mask(p.n).astype(np.complex128))
+    half = dataclasses.replace(p, n_slices=2, slice_dz=1.3)
+    full = dataclasses.replace(p, n_slices=1, slice_dz=2.6)
+    xy = np.array([[3.3, 7.1]])
+    psi = O.probe_k(p, xy)
+    a = O.multislice_k(half, np.ones((2, p.n, p.n), complex), psi)
+    b = O.multislice_k(full, np.ones((1, p.n, p.n), complex), psi)
+    assert np.allclose(a, b, atol=1e-12)

@@ -85,6 +85,14 @@ template <int N> struct ColCfg {
 template <int N>
 __device__ __forceinline__ bool in_band(int x) { return x <= N / 3 || x >= N - N / 3; }
 
+// Are all indices t + T q (0 <= t < T) outside the band limit?  With q known
+// after unrolling this is a constant, so the zeros it implies reach the first
+// FFT stage and the unused outputs of the last one are dropped.
+template <int N, int T>
+__device__ __forceinline__ constexpr bool all_out_of_band(int q) {
+  return q * T > N / 3 && q * T + T - 1 < N - N / 3;
+}
+
 __device__ __forceinline__ int signed_freq(int j, int n) { return j < (n >> 1) ? j : j - n; }
 
 // ---------------------------------------------------------------------------
@@ -163,7 +171,7 @@ __global__ void __launch_bounds__(RowCfg<N>::THREADS, RowCfg<N>::MINB) k_row_pas
 #pragma unroll
       for (int q = 0; q < E; ++q) {
         const int x = t + q * T;
-        v[q] = (!BAND_IN || in_band<N>(x)) ? w[x] : make_float2(0.0f, 0.0f);
+        v[q] = (!BAND_IN || (!all_out_of_band<N, T>(q) && in_band<N>(x))) ? w[x] : make_float2(0.0f, 0.0f);
       }
     }
 #if STEM_PREFETCH
@@ -215,7 +223,7 @@ __global__ void __launch_bounds__(RowCfg<N>::THREADS, RowCfg<N>::MINB) k_row_pas
 #pragma unroll
     for (int q = 0; q < E; ++q) {
       const int x = t + q * T;
-      if (!BAND_OUT || in_band<N>(x)) w[x] = v[q];
+      if (!BAND_OUT || (!all_out_of_band<N, T>(q) && in_band<N>(x))) w[x] = v[q];
     }
 
     if constexpr (MODE == ROW_IFFT_MAX) {
@@ -314,7 +322,7 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, ColCfg<N>::MINB) k_col_pas
       for (int q = 0; q < E; ++q) {
         const int ky = t + q * T;
         const int n = signed_freq(ky, N);
-        const bool keep = 9 * (m * m + n * n) <= N * N;
+        const bool keep = !all_out_of_band<N, T>(q) && 9 * (m * m + n * n) <= N * N;
         v[q] = keep ? cmul(v[q], cmul(px, __ldg(a.prop_y + ky))) : make_float2(0.0f, 0.0f);
       }
     }
@@ -451,7 +459,7 @@ __global__ void __launch_bounds__(ColTmaCfg<N_>::THREADS, ColTmaCfg<N_>::MINB)
     for (int q = 0; q < E; ++q) {
       const int ky = t + q * T;
       const int n = signed_freq(ky, N);
-      const bool keep = 9 * (m * m + n * n) <= N * N;
+      const bool keep = !all_out_of_band<N, T>(q) && 9 * (m * m + n * n) <= N * N;
       v[q] = keep ? cmul(v[q], cmul(px, __ldg(a.prop_y + ky))) : make_float2(0.0f, 0.0f);
     }
     fft_dist<N, true>(v, view, t, sync, tw);

@@ -364,15 +364,16 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, ColCfg<N>::MINB) k_col_pas
 }
 
 // ---------------------------------------------------------------------------
-// Slice-loop column pass of the large transforms moved by the tensor memory
-// accelerator.  A tile (C = 4 columns x N rows, 64 KB at N = 2048) reaches
-// shared memory as N / 256 2D tensor copies of 256 rows issued by one thread, one tile ahead of the
-// transform (two buffers, one mbarrier each), and leaves it the same way: the
-// transformed tile is written back into its buffer and stored by eight bulk
-// tensor copies, after which the buffer takes the tile after next.  The
-// threads issue no global loads or stores for the wave.  Every mbarrier wait
-// is bounded; on timeout the kernel records STEM_ERR_TIMEOUT in the status
-// word, waits (bounded) for its copies in flight and returns.
+// Slice-loop column pass of the large transforms (N = 1024, 2048) moved by the
+// tensor memory accelerator.  A tile (C = 4 columns x N rows, 64 KB at 2048)
+// reaches shared memory as N / 256 2D tensor copies of 256 rows issued by one
+// thread, one tile ahead of the transform (two buffers, one mbarrier each),
+// and leaves it the same way: the transformed tile is written back into its
+// buffer and stored by N / 256 bulk tensor copies, after which the buffer
+// takes the tile after next.  The threads issue no global loads or stores for
+// the wave.  Every mbarrier wait is bounded; on timeout the kernel records
+// STEM_ERR_TIMEOUT in the status word, waits (bounded) for its copies in
+// flight and returns.
 // ---------------------------------------------------------------------------
 #ifndef STEM_COL_TMA_MINB_1024
 #define STEM_COL_TMA_MINB_1024 2

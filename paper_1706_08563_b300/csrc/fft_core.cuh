@@ -286,4 +286,46 @@ __device__ __forceinline__ void fft_dist(float2 (&v)[FftShape<N>::E], const View
   }
 }
 
+// Two independent transforms of the same length (rows a and b) stage by stage,
+// sharing the barriers: the instructions of one fill the latencies of the
+// other, and a row costs half the barriers.  sa and sb are separate exchange
+// buffers.  Same register conventions as fft_dist.
+template <int N, bool INV, class View, class Sync>
+__device__ __forceinline__ void fft_dist_x2(float2 (&va)[FftShape<N>::E], float2 (&vb)[FftShape<N>::E],
+                                            const View& sa, const View& sb, int t, Sync sync, const float2* tw) {
+  using S = FftShape<N>;
+  using L = TwLayout<N>;
+  constexpr int E = S::E;
+  dft<E, INV>(va);
+  dft<E, INV>(vb);
+  if constexpr (S::R1 > 1) {
+    sync();
+#pragma unroll
+    for (int k = 0; k < E; ++k) {
+      sa.at(t * E + k) = va[k];
+      sb.at(t * E + k) = vb[k];
+    }
+    sync();
+    stage_load<N, E, S::R1>(va, sa, t);
+    stage_load<N, E, S::R1>(vb, sb, t);
+    stage_compute<N, E, S::R1, E, INV>(va, t, tw);
+    stage_compute<N, E, S::R1, E, INV>(vb, t, tw);
+    if constexpr (S::R2 > 1) {
+      sync();
+      stage_store<N, E, S::R1, E>(va, sa, t);
+      stage_store<N, E, S::R1, E>(vb, sb, t);
+      sync();
+      stage_load<N, E, S::R2>(va, sa, t);
+      stage_load<N, E, S::R2>(vb, sb, t);
+      stage_compute<N, E, S::R2, E * S::R1, INV>(va, t, tw + L::OFF2);
+      stage_compute<N, E, S::R2, E * S::R1, INV>(vb, t, tw + L::OFF2);
+      stage_rename<E, S::R2>(va);
+      stage_rename<E, S::R2>(vb);
+    } else {
+      stage_rename<E, S::R1>(va);
+      stage_rename<E, S::R1>(vb);
+    }
+  }
+}
+
 }  // namespace stem

@@ -238,6 +238,116 @@ __global__ void __launch_bounds__(RowCfg<N>::THREADS, RowCfg<N>::MINB) k_row_pas
 }
 
 // ---------------------------------------------------------------------------
+// Slice row pass at N = 2048 on pairs of waves: a tile is one row of two
+// neighbouring waves, transformed together (fft_dist_x2) against one staged
+// row of t_n.
+// ---------------------------------------------------------------------------
+#ifndef STEM_ROW_PAIR
+#define STEM_ROW_PAIR 1
+#endif
+#ifndef STEM_ROW_PAIR_MINB
+#define STEM_ROW_PAIR_MINB 3
+#endif
+struct RowPairCfg {
+  static constexpr int N = 2048, E = FftShape<N>::E, T = N / E, THREADS = T;
+  static constexpr int ROWBUF = N + N / E;
+  static constexpr size_t SMEM = ((size_t)2 * ROWBUF + TwLayout<N>::TOTAL + N) * sizeof(float2) + 16;
+};
+
+__global__ void __launch_bounds__(RowPairCfg::THREADS, STEM_ROW_PAIR_MINB)
+    k_row_slice_pair_2048(const PassArgs a, int n_tiles) {
+  using Cfg = RowPairCfg;
+  constexpr int N = Cfg::N, E = Cfg::E, T = Cfg::T;
+  extern __shared__ float2 smem[];
+  float2* xa = smem;
+  float2* xb = smem + Cfg::ROWBUF;
+  float2* tw = smem + 2 * Cfg::ROWBUF;
+  float2* tbuf = tw + TwLayout<N>::TOTAL;
+  uint64_t* tbar = reinterpret_cast<uint64_t*>(tbuf + N);
+  if (threadIdx.x == 0) {
+    mbar_init(smem_u32(tbar), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  build_twiddles<N>(tw, threadIdx.x, Cfg::THREADS);
+  __syncthreads();
+  const int t = threadIdx.x;
+  const SmemView<E, 1> va{xa}, vb{xb};
+  auto sync = [] { __syncthreads(); };
+  const int pairs = (a.batch + 1) / 2;
+  const int per = (n_tiles + gridDim.x - 1) / gridDim.x;
+  const int tile_end = min(n_tiles, (int)(blockIdx.x + 1) * per);
+  int staged_row = -1;
+  uint32_t tphase = 0;
+
+  for (int tile = blockIdx.x * per; tile < tile_end; ++tile) {
+    const int row = tile / pairs, k = tile % pairs;
+    const int wa = 2 * k, wb = 2 * k + 1;
+    const bool has_b = wb < a.batch;
+    float2* pa = a.wave + (size_t)wa * N * N + (size_t)row * N;
+    float2* pb = a.wave + (size_t)(has_b ? wb : wa) * N * N + (size_t)row * N;
+    const bool fresh = row != staged_row;
+    if (fresh) {
+      __syncthreads();   // every thread has read the previous row of t_n
+      if (threadIdx.x == 0) {
+        fence_proxy_async();
+        const uint32_t bar = smem_u32(tbar);
+        mbar_arrive_expect_tx(bar, N * (uint32_t)sizeof(float2));
+        bulk_load(smem_u32(tbuf), a.trans + (size_t)row * N, N * (uint32_t)sizeof(float2), bar);
+      }
+    }
+    float2 A[E], B[E];
+#pragma unroll
+    for (int q = 0; q < E; ++q) {
+      const int x = t + q * T;
+      const bool in = !all_out_of_band<N, T>(q) && in_band<N>(x);
+      A[q] = in ? pa[x] : make_float2(0.0f, 0.0f);
+      B[q] = (in && has_b) ? pb[x] : make_float2(0.0f, 0.0f);
+    }
+#if STEM_PREFETCH
+    if (t == 0 && tile + 1 < tile_end) {
+      const int nrow = (tile + 1) / pairs, nk = (tile + 1) % pairs;
+      constexpr int lo = ((N / 3 + 1) + 1) & ~1, hi = (N - N / 3) & ~1;
+      for (int j = 0; j < 2; ++j) {
+        const int nw = 2 * nk + j;
+        if (nw >= a.batch) break;
+        const float2* nr = a.wave + (size_t)nw * N * N + (size_t)nrow * N;
+        prefetch_l2_bulk(nr, lo * sizeof(float2));
+        prefetch_l2_bulk(nr + hi, (N - hi) * sizeof(float2));
+      }
+    }
+#endif
+    fft_dist_x2<N, true>(A, B, va, vb, t, sync, tw);
+    if (fresh) {
+      const bool ok = mbar_wait(smem_u32(tbar), tphase);
+      tphase ^= 1u;
+      staged_row = row;
+      if (__syncthreads_or(!ok)) {
+        if (threadIdx.x == 0) {
+          if (a.status) atomicExch(a.status, (int)STEM_ERR_TIMEOUT);
+          mbar_wait(smem_u32(tbar), tphase ^ 1u);   // let the copy land before the CTA exits
+        }
+        return;
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < E; ++q) {
+      const float2 tv = tbuf[t + q * T];
+      A[q] = cmul(A[q], tv);
+      B[q] = cmul(B[q], tv);
+    }
+    fft_dist_x2<N, false>(A, B, va, vb, t, sync, tw);
+#pragma unroll
+    for (int q = 0; q < E; ++q) {
+      const int x = t + q * T;
+      if (!all_out_of_band<N, T>(q) && in_band<N>(x)) {
+        pa[x] = A[q];
+        if (has_b) pb[x] = B[q];
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Column pass: persistent CTAs over tiles of C columns of one wave.  Thread
 // (c, t) = threadIdx c + C t holds column elements t + T q; neighbouring lanes
 // read neighbouring columns, so every global access is C * 8 contiguous bytes.
@@ -544,8 +654,24 @@ static cudaError_t col_launch(const PassArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+static cudaError_t row_slice_pair_2048(const PassArgs& a, cudaStream_t s) {
+  using Cfg = RowPairCfg;
+  static std::once_flag flag, occ_flag;
+  static int occ = 0;
+  cudaError_t e = set_smem(k_row_slice_pair_2048, Cfg::SMEM, flag);
+  if (e != cudaSuccess) return e;
+  const int n_tiles = ((a.batch + 1) / 2) * Cfg::N;
+  const int grid = std::min(n_tiles, resident_ctas(k_row_slice_pair_2048, Cfg::THREADS, Cfg::SMEM, occ_flag, occ));
+  note_launch(), k_row_slice_pair_2048<<<grid, Cfg::THREADS, Cfg::SMEM, s>>>(a, n_tiles);
+  return cudaGetLastError();
+}
+
 template <int N>
 static cudaError_t row_dispatch(int mode, const PassArgs& a, cudaStream_t s) {
+#if STEM_ROW_PAIR
+  if constexpr (N == 2048)
+    if (mode == ROW_SLICE) return row_slice_pair_2048(a, s);
+#endif
   switch (mode) {
     case ROW_FFT: return row_launch<N, ROW_FFT>(a, s);
     case ROW_IFFT: return row_launch<N, ROW_IFFT>(a, s);

@@ -37,7 +37,7 @@ METRIC = "probes/s for multislice and PRISM f=8 at stated error; p50/p99 solve l
 # DRAM bytes per wave and slice (row + column pass, t_n excluded), measured
 # with ncu (dram__bytes_read.sum + dram__bytes_write.sum) on launches of 16
 # waves of 2048^2 and 32 waves of 1024^2 of the current slice passes
-SLICE_TRAFFIC_PER_WAVE = {2048: 82.93e6, 1024: 19.33e6}
+SLICE_TRAFFIC_PER_WAVE = {2048: 83.09e6, 1024: 19.33e6}
 HBM_FALLBACK_GBS = 6400.0
 
 
@@ -266,16 +266,18 @@ def run_ours(args, rank, world, local_rank):
         alg = (n_beams * (w.n_slices * 32.0 * band + 8.0 * band + 8.0 + 8.0 + 2.0 * esz) * n2
                + nbatches * w.n_slices * 8.0 * n2)
         ms = statistics.mean(sm_ms)
-        kernel = (f"k_row_pass<{w.n}> + k_col_slice_tma<{w.n}> (S-matrix slice passes)" if w.n >= 1024
-                  else f"k_row_pass/k_col_pass<{w.n}> (S-matrix slice passes)")
+        kernel = {2048: "k_row_slice_pair_2048 + k_col_slice_tma<2048> (S-matrix slice passes)",
+                  1024: "k_row_pass<1024> + k_col_slice_tma<1024> (S-matrix slice passes)"}.get(
+                      w.n, f"k_row_pass/k_col_pass<{w.n}> (S-matrix slice passes)")
     else:
         nb = math.ceil(n_probes / batch)
         # per probe: init write, then per slice row + column pass, the last column
         # pass reads only (detector): 32 S B per in-band pixel; t_n once per batch
         alg = n_probes * w.n_slices * 32.0 * band * n2 + nb * w.n_slices * 8.0 * n2
         ms = statistics.mean(out_ms)
-        kernel = (f"k_row_pass<{w.n}> + k_col_slice_tma<{w.n}> (multislice slice passes)" if w.n >= 1024
-                  else f"k_row_pass/k_col_pass<{w.n}> (multislice slice passes)")
+        kernel = {2048: "k_row_slice_pair_2048 + k_col_slice_tma<2048> (multislice slice passes)",
+                  1024: "k_row_pass<1024> + k_col_slice_tma<1024> (multislice slice passes)"}.get(
+                      w.n, f"k_row_pass/k_col_pass<{w.n}> (multislice slice passes)")
     ach = alg / (ms / 1e3) / 1e9
     per_wave = SLICE_TRAFFIC_PER_WAVE.get(w.n)
     waves = n_beams if prism else n_probes

@@ -192,7 +192,9 @@ stem_status stem_multislice_scan_4d(stem_plan plan, const void* trans, const dou
  * device current); make that first call before any stream capture.  Every call
  * shares the array: calls that overlap on the GPU (other streams, other host
  * threads) race and corrupt each other's waves; serialise them.  No call
- * allocates, and nothing in the array needs clearing between calls. */
+ * allocates, and nothing in the array needs clearing between calls.  The
+ * device current at the call must be the plan's device (the one current at
+ * stem_plan_create), else STEM_ERR_INVALID and nothing is launched. */
 stem_status stem_multislice_scan_noalloc(stem_plan plan, const void* trans, const double* probe_xy,
                                          int64_t n_probes, int32_t batch, float weight,
                                          float* rings_out, void* stream);

@@ -45,14 +45,22 @@ extern "C" stem_status stem_multislice_scan_noalloc(stem_plan plan, const void* 
                                                     int64_t n_probes, int32_t batch, float weight,
                                                     float* rings_out, void* stream) {
   if (!plan || batch < 1) return STEM_ERR_INVALID;
+  // The plan's tables live on the device that was current at stem_plan_create,
+  // and the scratch address looked up below belongs to the current device:
+  // with another device current the kernels would mix memory of two devices.
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return STEM_ERR_CUDA;
+  if (dev != plan->device) return STEM_ERR_INVALID;
   const size_t need = stem_multislice_workspace(plan, batch);
   if (need == 0) return STEM_ERR_INVALID;
   if (need > kNoAllocScratchBytes) return STEM_ERR_NOMEM;
   void* scratch = nullptr;
   const stem_status st = scratch_address(&scratch);
   if (st != STEM_OK) return st;
-  // The waves are fully written by the probe-initialisation pass before any
-  // read, so the scratch needs no clearing between calls.
+  // No clearing between calls is needed: the probe-initialisation pass writes
+  // every in-band column of each wave, and the out-of-band columns, which keep
+  // whatever an earlier call left there, are masked to zero by every pass that
+  // reads them.
   return stem_multislice_scan(plan, trans, probe_xy, n_probes, batch, weight, rings_out, scratch,
                               kNoAllocScratchBytes, stream);
 }

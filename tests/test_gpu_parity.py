@@ -156,7 +156,7 @@ def test_multislice_empty_and_errors(api):
 
 # --------------------------------------------------------------------- PRISM
 def _small_prism_case(n=128, f=4, slices=4, atoms=60, seed=21):
-    w = W.Workload("p", (24.0, 24.0, 8.0), atoms, n, slices, 2.0, 200.0, 20.0, 8, 2.0, 60, f=(f,))
+    w = W.Workload("p", (24.0, 28.0, 8.0), atoms, n, slices, 2.0, 200.0, 20.0, 8, 2.0, 60, f=(f,))
     xyz, gauss = W.atoms(w, seed=seed)
     return w, xyz, gauss
 

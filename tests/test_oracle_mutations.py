@@ -101,6 +101,20 @@ def _chi_cs_no_lambda_cubed(p, kx, ky):
     return math.pi * p.lam * p.defocus * k2 + 0.5 * math.pi * p.cs * p.lam * k2 * k2
 
 
+def _window_crop_axes_swapped(p, smatrix, beams, f, xy):
+    # the window's rows taken from the x origin and its columns from the y origin
+    w = p.n // f
+    org = O.prism_window_origin(p, f, xy)
+    coef = O.prism_coefficients(p, beams, xy)
+    out = np.empty((org.shape[0], w, w), dtype=np.complex128)
+    u = np.arange(w)
+    for i in range(org.shape[0]):
+        rows = np.mod(org[i, 0] + u, p.n)
+        cols = np.mod(org[i, 1] + u, p.n)
+        out[i] = np.tensordot(coef[i], smatrix[:, rows][:, :, cols], axes=(0, 0))
+    return out
+
+
 def _fp_first_config_only(p, configs, gauss, xy, algo="ms", f=1):
     # every configuration replaced by the first one
     return O._orig_frozen_phonon_rings(p, [configs[0]] * len(configs), gauss, xy, algo, f)
@@ -120,6 +134,9 @@ CASES = [
     ("probe_k", _probe_unnormalised, [pins.test_probe_normalisation_and_free_space_rings]),
     ("prism_window_origin", _origin_round_down, [pins.test_prism_window_origin]),
     ("prism_coefficients", _coef_conj, [pins.test_prism_f1_equals_multislice]),
+    ("prism_window_waves", _window_crop_axes_swapped,
+     [lambda: pins.test_prism_shift_covariance_non_square_cell(2),
+      lambda: pins.test_prism_shift_covariance_non_square_cell(4)]),
     ("slice_index", _slice_round, [pins.test_slice_assignment]),
     ("projected_potential", _potential_one_gaussian, [pins.test_potential_sum_rule_and_peak]),
     ("wavelength", _lambda_nonrel, [pins.test_wavelength_textbook_values]),
@@ -135,5 +152,5 @@ CASES = [
 def test_pins_catch_planted_mistake(monkeypatch, name, mutant, checks):
     monkeypatch.setattr(O, "_orig_" + name, getattr(O, name), raising=False)
     monkeypatch.setattr(O, name, mutant)
-    caught = [c.__name__ for c in checks if _fails(c)]
+    caught = [getattr(c, "__name__", "check") for c in checks if _fails(c)]
     assert caught, f"no pin caught the mutation {mutant.__name__} of {name}"

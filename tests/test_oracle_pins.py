@@ -349,6 +349,44 @@ def test_prism_window_origin():
     assert org.tolist() == [[56, 56], [57, 56], [(64 - 8) % 64, 24]]
 
 
+@pytest.mark.parametrize("f", [2, 4])
+def test_prism_shift_covariance_non_square_cell(f):
+    """Moving every atom by whole pixels (a dx, b dy) with a != b in a cell with
+    Lx != Ly and the probes by the same vector leaves the PRISM window waves
+    unchanged: each exit wave becomes S_b(r - s) exp(2 pi i k_b . s), the
+    coefficient picks up exp(-2 pi i k_b . s) and the window origin moves by
+    (a, b) pixels.  This fixes which axis of the window crop follows x and
+    which follows y (a crop with the axes exchanged moves the window by (b, a)
+    and fails), which neither f = 1 nor free space can see."""
+    p = O.Params((10.0, 13.0, 4.0), 32, 2, 2.0, 200.0, 30.0, 4.0, 40)
+    rng = np.random.default_rng(61)
+    xyz = rng.random((14, 3)) * np.array(p.cell)
+    gauss = np.tile(np.array([5.0, 0.2, 2.0, 0.6], np.float32), (14, 1))
+    a, b = 3, -5
+    shift = np.array([a * p.dx, b * p.dy, 0.0])
+    xyz2 = xyz + shift
+    xyz2[:, 0] %= p.cell[0]
+    xyz2[:, 1] %= p.cell[1]
+    t1 = O.transmission(p, O.projected_potential(p, xyz, gauss))
+    t2 = O.transmission(p, O.projected_potential(p, xyz2, gauss))
+    beams = O.prism_beams(p, f)
+    s1 = O.prism_smatrix(p, t1, beams)
+    s2 = O.prism_smatrix(p, t2, beams)
+    # probe positions a quarter pixel off the rounding boundary of the origin
+    xy = np.array([[1.1 * p.dx, 2.3 * p.dy], [20.2 * p.dx, 7.9 * p.dy], [30.7 * p.dx, 25.4 * p.dy]])
+    xy2 = xy + shift[:2]
+    assert np.array_equal(O.prism_window_origin(p, f, xy2),
+                          np.mod(O.prism_window_origin(p, f, xy) + np.array([a, b]), p.n))
+    w1 = O.prism_window_waves(p, s1, beams, f, xy)
+    w2 = O.prism_window_waves(p, s2, beams, f, xy2)
+    assert np.max(np.abs(w1 - w2)) < 1e-10 * np.max(np.abs(w1))
+    r1 = O.prism_rings(p, s1, beams, f, xy)
+    r2 = O.prism_rings(p, s2, beams, f, xy2)
+    assert np.max(np.abs(r1 - r2)) < 1e-10 * np.max(r1)
+    # the shift does change the window waves at a fixed probe position
+    assert np.max(np.abs(O.prism_window_waves(p, s2, beams, f, xy) - w1)) > 1e-3 * np.max(np.abs(w1))
+
+
 # -------------------------------------------------------------- aberrations
 def test_defocus_equals_free_propagation():
     """A probe with defocus C1 is the in-focus probe propagated by C1 with Eq. 2's

@@ -4,7 +4,8 @@
 // intensity in Fourier space summed over virtual detectors; here an array of
 // annular rings (the 3D output).  The ring of each Fourier pixel comes from the
 // plan's look-up table (decided once in FP64 on the host); a CTA sums |psi|^2
-// into shared-memory rings and adds them to the output once.
+// into shared-memory rings, a warp's run of equal rings by shuffles first
+// (warp_run_add), and adds them to the output once.
 #include "fft_core.cuh"
 #include "internal.h"
 
@@ -22,9 +23,11 @@ __global__ void __launch_bounds__(kReadThreads) k_readout(const float2* __restri
   __syncthreads();
   const float2* src = psi + b * npix;
   const int64_t p0 = (int64_t)blockIdx.x * kReadPix;
-  for (int64_t p = p0 + threadIdx.x; p < p0 + kReadPix && p < npix; p += kReadThreads) {
-    const int r = __ldg(lut + p) & kLutNoRing;
-    if (r != kLutNoRing) atomicAdd(acc + r, cabs2(src[p]));
+  // consecutive lanes take consecutive pixels of a row, whose rings form runs
+  for (int64_t p = p0 + threadIdx.x; p < p0 + kReadPix; p += kReadThreads) {
+    const bool in = p < npix;
+    const int r = in ? (__ldg(lut + p) & kLutNoRing) : kLutNoRing;
+    warp_run_add(acc, r, in ? cabs2(src[p]) : 0.0f, kLutNoRing);
   }
   __syncthreads();
   for (int i = threadIdx.x; i < n_rings; i += kReadThreads)

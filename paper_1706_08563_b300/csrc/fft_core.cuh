@@ -328,4 +328,28 @@ __device__ __forceinline__ void fft_dist_x2(float2 (&va)[FftShape<N>::E], float2
   }
 }
 
+// Ring accumulation with warp primitives: each of the 32 lanes of a warp adds
+// v into acc[key].  Lanes whose keys form a run of equal values in lane order
+// are summed first by a segmented inclusive scan over shuffles, and the last
+// lane of each run issues the one shared-memory atomic of that run (keys equal
+// to skip_key are dropped).  Any arrangement of keys gives the right sums; runs
+// make it cheap, and along a column or row of an FFT grid the ring index is
+// monotonic on each half, so neighbouring lanes mostly share a ring.  All 32
+// lanes must call it together.
+__device__ __forceinline__ void warp_run_add(float* acc, int key, float v, int skip_key) {
+  const unsigned lane = threadIdx.x & 31u;
+  const int prev = __shfl_up_sync(0xffffffffu, key, 1);
+  const unsigned heads = __ballot_sync(0xffffffffu, lane == 0u || prev != key);
+  // first lane of this lane's run: the highest head at or below it
+  const int start = 31 - __clz(heads & (0xffffffffu >> (31u - lane)));
+  float s = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const float u = __shfl_up_sync(0xffffffffu, s, o);
+    if ((int)lane - o >= start) s += u;
+  }
+  const bool tail = lane == 31u || ((heads >> (lane + 1u)) & 1u);
+  if (tail && key != skip_key) atomicAdd(acc + key, s);
+}
+
 }  // namespace stem

@@ -441,12 +441,36 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, ColCfg<N>::MINB) k_col_pas
       fft_dist<N, true>(v, view, t, sync, tw);
 
     if constexpr (MODE == COL_DET) {
-      __syncthreads();   // ring_acc zeroed
+      __syncthreads();   // ring_acc zeroed; every thread is done with the exchange buffer
+      if constexpr (Cfg::THREADS >= 32) {
+        // (|psi|^2, ring) of the tile, column by column in row order, in the
+        // exchange buffer (row stride S keeps the scattered writes free of bank
+        // conflicts); then each warp takes runs of 32 consecutive rows of one
+        // column, along which the ring index changes rarely (warp_run_add)
+        constexpr int S = N + 16 / C;
+        float2* pk = smem;
 #pragma unroll
-      for (int q = 0; q < E; ++q) {
-        const int ky = t + q * T;
-        const int r = __ldg(a.lut + (size_t)ky * N + col) & kLutNoRing;
-        if (r != kLutNoRing) atomicAdd(ring_acc + r, cabs2(v[q]));
+        for (int q = 0; q < E; ++q) {
+          const int ky = t + q * T;
+          const int r = __ldg(a.lut + (size_t)ky * N + col) & kLutNoRing;
+          pk[c * S + ky] = make_float2(cabs2(v[q]), __int_as_float(r));
+        }
+        __syncthreads();
+        constexpr int NW = Cfg::THREADS / 32;
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll 4
+        for (int i = 0; i < E; ++i) {        // C * N / 32 runs of 32 elements, E per warp
+          const int idx = (warp + NW * i) * 32 + lane;
+          const float2 e = pk[(idx / N) * S + idx % N];
+          warp_run_add(ring_acc, __float_as_int(e.y), e.x, kLutNoRing);
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < E; ++q) {
+          const int ky = t + q * T;
+          const int r = __ldg(a.lut + (size_t)ky * N + col) & kLutNoRing;
+          if (r != kLutNoRing) atomicAdd(ring_acc + r, cabs2(v[q]));
+        }
       }
       __syncthreads();
       float* out = a.rings + (size_t)wave * a.n_rings;

@@ -135,6 +135,17 @@ stem_status stem_plan_device_status(stem_plan plan, int32_t* code);
  * STEM_ERR_INVALID for a null plan or a limit out of range. */
 stem_status stem_selftest_bounded_wait(stem_plan plan, int64_t limit_ns, void* stream);
 
+/* FP32 arithmetic rate probe; the paper has no counterpart.  It gives the
+ * measured denominator of the FP32 roofline of the FFT passes.  Launches
+ * `blocks` CTAs of 256 threads; each thread runs `iters` rounds of 8
+ * independent FMA chains: scalar FMAs (packed = 0; one lane operation each)
+ * or the packed f32x2 FMA (packed = 1; two lane operations each).  Lane
+ * operations per launch = blocks * 256 * iters * 8 * (packed ? 2 : 1); the
+ * caller times the launch on `stream`.  out: float32 [blocks * 256] device
+ * buffer (written with one sum per thread).  STEM_ERR_INVALID for iters < 1,
+ * blocks outside [1, 2^20] or a NULL out; asynchronous. */
+stem_status stem_selftest_fma_rate(int32_t packed, int64_t iters, int32_t blocks, float* out, void* stream);
+
 /* ---------------------------------------------------------------------------
  * Projected potentials (Methods, "Calculation of the Projected Potentials").
  * The paper's Kirkland look-up table is replaced by a sum of two isotropic

@@ -334,7 +334,16 @@ def prism_coefficients(p: Params, beams: np.ndarray, xy: np.ndarray) -> np.ndarr
     return np.exp(-2j * math.pi * ph - 1j * chi[None, :]) / math.sqrt(beams.shape[0])
 
 
-def prism_window_waves(p: Params, smatrix: np.ndarray, beams: np.ndarray, f: int,
+def _smatrix_crop(smatrix, rows: np.ndarray, cols: np.ndarray) -> np.ndarray:
+    """S_b on the given rows (y) and columns (x) of the grid, [n_b, len(rows), len(cols)].
+    `smatrix` is an array [n_b, N, N], or any object whose crop(rows, cols) returns
+    that sub-array (an S-matrix too large to hold whole, read window by window)."""
+    if hasattr(smatrix, "crop"):
+        return np.asarray(smatrix.crop(rows, cols), dtype=np.complex128)
+    return smatrix[:, rows][:, :, cols]
+
+
+def prism_window_waves(p: Params, smatrix, beams: np.ndarray, f: int,
                        xy: np.ndarray) -> np.ndarray:
     """Psi_p(v, u) = sum_b c[p, b] S_b((o_p + (u, v)) mod N), [P, W, W] (rows v, cols u)."""
     w = p.n // f
@@ -345,12 +354,12 @@ def prism_window_waves(p: Params, smatrix: np.ndarray, beams: np.ndarray, f: int
     for i in range(org.shape[0]):
         rows = np.mod(org[i, 1] + u, p.n)
         cols = np.mod(org[i, 0] + u, p.n)
-        crop = smatrix[:, rows][:, :, cols]                  # [n_b, W, W]
+        crop = _smatrix_crop(smatrix, rows, cols)            # [n_b, W, W]
         out[i] = np.tensordot(coef[i], crop, axes=(0, 0))
     return out
 
 
-def prism_dp(p: Params, smatrix: np.ndarray, beams: np.ndarray, f: int, xy: np.ndarray) -> np.ndarray:
+def prism_dp(p: Params, smatrix, beams: np.ndarray, f: int, xy: np.ndarray) -> np.ndarray:
     """PRISM 4D output on the window grid: |FFT_W(Psi_p)|^2 / W^4 inside the band
     limit (coarse (mu, nu) standing for (f mu, f nu)), [P, W, W] in FFT order."""
     w = p.n // f
@@ -358,7 +367,7 @@ def prism_dp(p: Params, smatrix: np.ndarray, beams: np.ndarray, f: int, xy: np.n
     return np.abs(spec) ** 2 / float(w) ** 4 * bandlimit_mask(w)[None]
 
 
-def prism_rings(p: Params, smatrix: np.ndarray, beams: np.ndarray, f: int,
+def prism_rings(p: Params, smatrix, beams: np.ndarray, f: int,
                 xy: np.ndarray, chunk: int = 64) -> np.ndarray:
     """PRISM annular-ring output [P, n_rings]: window beam sum, W x W FFT, |.|^2 / W^4,
     binned on the coarse grid."""

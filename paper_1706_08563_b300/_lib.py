@@ -44,6 +44,7 @@ SIGNATURES = {
     "stem_plan_destroy": (None, [c_void_p]),
     "stem_plan_device_status": (c_int32, [c_void_p, POINTER(c_int32)]),
     "stem_selftest_bounded_wait": (c_int32, [c_void_p, c_int64, c_void_p]),
+    "stem_selftest_fma_rate": (c_int32, [c_int32, c_int64, c_int32, c_void_p, c_void_p]),
     "stem_plan_constants": (c_int32, [c_void_p, POINTER(c_double), POINTER(c_double), POINTER(c_int32)]),
     "stem_slice_potentials_workspace": (c_size_t, [c_void_p, c_int64]),
     "stem_slice_potentials": (c_int32, [c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_void_p, c_void_p,

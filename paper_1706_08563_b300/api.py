@@ -80,6 +80,19 @@ class SMatrix:
         c = torch.complex(d[:, :, 0, :], d[:, :, 1, :])
         return c.permute(2, 0, 1)[: self.n_beams].contiguous()
 
+    def crop(self, rows, cols) -> np.ndarray:
+        """S_b(y, x) over the given rows and columns, copied to the host as
+        complex128 [n_beams, len(rows), len(cols)] (stored values times s_b).
+        An inspection accessor: it reads one window at a time, for checks of
+        the output step against an independent implementation, without
+        holding the whole S-matrix on the host."""
+        d = self.data()
+        r = torch.as_tensor(np.asarray(rows, dtype=np.int64), device=d.device)
+        c = torch.as_tensor(np.asarray(cols, dtype=np.int64), device=d.device)
+        sub = d.index_select(0, r).index_select(1, c)[..., : self.n_beams].double()
+        sub = sub * self.scales()[: self.n_beams].double()[None, None, None, :]
+        return torch.complex(sub[:, :, 0, :], sub[:, :, 1, :]).permute(2, 0, 1).contiguous().cpu().numpy()
+
     def save(self, path: str, plan: "Plan", tag: str = "") -> None:
         """Checkpoint the S-matrix to a file (.npz): the raw buffer plus the plan
         parameters it depends on, so that ``Plan.load_smatrix`` can refuse a

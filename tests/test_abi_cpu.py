@@ -135,6 +135,9 @@ def test_streamed_entry_points_reject_bad_arguments():
 def test_selftest_entry_point_rejects_bad_arguments():
     lib = _lib.load()
     assert lib.stem_selftest_bounded_wait(None, 1000, None) == _lib.STEM_ERR_INVALID
+    assert lib.stem_selftest_fma_rate(0, 0, 1, ctypes.c_void_p(16), None) == _lib.STEM_ERR_INVALID
+    assert lib.stem_selftest_fma_rate(1, 10, 0, ctypes.c_void_p(16), None) == _lib.STEM_ERR_INVALID
+    assert lib.stem_selftest_fma_rate(0, 10, 1, None, None) == _lib.STEM_ERR_INVALID
 
 
 def test_c_client_compiles_and_links_as_c99(repo_tmp):

@@ -7,7 +7,8 @@ on outputs the FP64 oracle can compute one by one.
   with the tcgen05 beam sum and chunks of 4096 probes: the potentials on
   sampled slices, two sampled S-matrix beams against the oracle (through all
   100 slices), and the output of 33 sampled probes computed by the oracle from
-  the GPU's own S-matrix (stage-wise: it isolates the output step).
+  the GPU's own S-matrix, read window by window (stage-wise: it isolates the
+  output step).
 """
 import numpy as np
 import pytest
@@ -84,25 +85,15 @@ def test_prism8_smatrix_sampled_beams(prism8):
 
 def test_prism8_output_sampled_probes(prism8):
     """Rings of sampled probes (bench chunk of 4096, tcgen05 engine) against the
-    oracle's output step applied to the GPU's own S-matrix."""
+    oracle's output step (window crop, beam sum, window FFT, rings) applied to
+    the GPU's own S-matrix, read window by window."""
     w, xyz, gauss, plan, trans, v, sm = prism8
     p = O.params_from(w)
     beams = O.prism_beams(p, 8)
     xy_all = W.scan_positions(w)[:4096]
     rings = plan.prism_output(sm, torch.from_numpy(xy_all).cuda(), chunk=4096).cpu().numpy()
-    wdw = p.n // 8
-    sc = sm.scales()
-    for i in list(range(0, 4096, 128)) + [4095]:      # 33 probes over the chunk's 16 scan rows
-        xy = xy_all[i:i + 1]
-        o = O.prism_window_origin(p, 8, xy)[0]
-        rows = torch.from_numpy(np.mod(o[1] + np.arange(wdw), p.n)).cuda()
-        cols = torch.from_numpy(np.mod(o[0] + np.arange(wdw), p.n)).cuda()
-        crop = sm.data()[rows][:, cols].float() * sc[None, None, None, :]       # [W, W, 2, nbp]
-        s_win = torch.complex(crop[:, :, 0, : len(beams)], crop[:, :, 1, : len(beams)]).permute(2, 0, 1)
-        s_win = s_win.cpu().numpy().astype(np.complex128)
-        coef = O.prism_coefficients(p, beams, xy)[0]
-        psi = np.tensordot(coef, s_win, axes=(0, 0))
-        spec = np.abs(np.fft.fft2(psi)) ** 2 / float(wdw) ** 4
-        ref = O.detector_rings(O.coarse_ring_table(p, 8), p.n_rings, spec[None])[0]
-        got = rings[i]
-        assert _rel(got, ref) <= 1e-2, i
+    pick = np.array(list(range(0, 4096, 128)) + [4095])      # 33 probes over the chunk's 16 scan rows
+    ref = O.prism_rings(p, sm, beams, 8, xy_all[pick])
+    for k, i in enumerate(pick):
+        assert _rel(rings[i], ref[k]) <= 1e-2, i
+    check_rings(rings[pick], ref, 1e-2)

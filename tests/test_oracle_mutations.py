@@ -111,7 +111,7 @@ def _window_crop_axes_swapped(p, smatrix, beams, f, xy):
     for i in range(org.shape[0]):
         rows = np.mod(org[i, 0] + u, p.n)
         cols = np.mod(org[i, 1] + u, p.n)
-        out[i] = np.tensordot(coef[i], smatrix[:, rows][:, :, cols], axes=(0, 0))
+        out[i] = np.tensordot(coef[i], O._smatrix_crop(smatrix, rows, cols), axes=(0, 0))
     return out
 
 

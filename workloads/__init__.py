@@ -129,42 +129,6 @@ def random_complex(shape, seed: int, dtype=np.complex128) -> np.ndarray:
 
 
 @dataclasses.dataclass
-class Request:
-    """One serving request (a whole simulation on its own atoms)."""
-    rid: int
-    arrival_s: float
-    kind: str            # "ms" or "prism"
-    workload: Workload
-    f: int = 1
-
-
-def serving_stream(n_requests: int, rate_hz: float, seed: int = ARRIVAL_SEED,
-                   grids: Tuple[int, ...] = (256, 512, 1024, 2048),
-                   fs: Tuple[int, ...] = (1, 2, 4, 8, 16),
-                   scans: Tuple[int, ...] = (16, 32, 64, 128, 256),
-                   slices: Tuple[int, int] = (10, 100),
-                   cell: float = 100.0, n_atoms: int = 50000) -> List[Request]:
-    """Seeded Poisson arrivals of mixed multislice / PRISM requests."""
-    rng = np.random.default_rng(seed)
-    t = 0.0
-    out = []
-    for i in range(n_requests):
-        t += rng.exponential(1.0 / rate_hz)
-        kind = "prism" if rng.random() < 0.5 else "ms"
-        n = int(rng.choice(grids))
-        s = int(rng.integers(slices[0], slices[1] + 1))
-        scan = int(rng.choice(scans))
-        f = int(rng.choice(fs)) if kind == "prism" else 1
-        # keep the window at least 8 pixels wide
-        while kind == "prism" and n // f < 8:
-            f //= 2
-        w = Workload(f"req{i}", (cell, cell, cell), n_atoms, n, s, cell / s, 200.0, 20.0,
-                     scan, 1.0, 100)
-        out.append(Request(i, t, kind, w, f))
-    return out
-
-
-@dataclasses.dataclass
 class Recipe:
     """A specimen plus fixed simulation settings that several requests share."""
     specimen: str
@@ -176,26 +140,32 @@ class Recipe:
 
 
 def serving_recipes(grids: Tuple[int, ...] = (256, 512), cell: float = 50.0, n_atoms: int = 6000,
-                    seed: int = ARRIVAL_SEED, count: int = 6) -> List[Recipe]:
-    """Seeded mix of multislice and PRISM settings (grid, slice count, f, storage)."""
+                    seed: int = ARRIVAL_SEED, count: int = 6, fs: Tuple[int, ...] = (4, 8, 16),
+                    slices: Tuple[int, int] = (10, 40)) -> List[Recipe]:
+    """Seeded mix of multislice and PRISM settings (grid, slice count in the
+    inclusive range `slices`, f from `fs` with the window W = N / f kept at 8 or
+    more, storage)."""
     rng = np.random.default_rng(seed)
     out = []
     for i in range(count):
         n = int(rng.choice(grids))
-        slices = int(rng.integers(10, 41))
+        n_sl = int(rng.integers(slices[0], slices[1] + 1))
         algo = "prism" if i % 2 else "ms"
-        f = int(rng.choice((4, 8, 16))) if algo == "prism" else 1
+        f = int(rng.choice(fs)) if algo == "prism" else 1
+        while n // f < 8:
+            f //= 2
         storage = str(rng.choice(("f16", "bf16", "f32"))) if algo == "prism" else "f32"
-        w = Workload(f"spec{i}", (cell, cell, slices * 1.0), n_atoms * slices // 40, n, slices, 1.0, 200.0,
+        w = Workload(f"spec{i}", (cell, cell, n_sl * 1.0), n_atoms * n_sl // 40, n, n_sl, 1.0, 200.0,
                      20.0, 16, 1.0, 100)
         out.append(Recipe(f"spec{i}", w, algo, f, storage, seed + 1 + i))
     return out
 
 
 def serving_requests(recipes: List[Recipe], n_requests: int, rate_hz: float, seed: int = ARRIVAL_SEED,
-                     scans: Tuple[int, ...] = (8, 16, 32)):
+                     scans: Tuple[int, ...] = (8, 16, 32), max_scan: Optional[List[int]] = None):
     """Poisson arrivals; each request scans a random square region of one recipe's
-    specimen.  Returns [(arrival_s, recipe_index, probe_xy float64 [P, 2])]."""
+    specimen (side drawn from `scans`, halved while above max_scan[recipe] when
+    given).  Returns [(arrival_s, recipe_index, probe_xy float64 [P, 2])]."""
     rng = np.random.default_rng(seed + 99)
     t = 0.0
     out = []
@@ -204,6 +174,8 @@ def serving_requests(recipes: List[Recipe], n_requests: int, rate_hz: float, see
         k = int(rng.integers(len(recipes)))
         w = recipes[k].workload
         s = int(rng.choice(scans))
+        while max_scan is not None and s > max(1, max_scan[k]):
+            s //= 2
         step = w.cell[0] / 64.0
         x0, y0 = rng.random(2) * np.asarray(w.cell[:2])
         g = np.arange(s) * step

@@ -507,7 +507,9 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, ColCfg<N>::MINB) k_col_pas
 // takes the tile after next.  The threads issue no global loads or stores for
 // the wave.  Every mbarrier wait is bounded; on timeout the kernel records
 // STEM_ERR_TIMEOUT in the status word, waits (bounded) for its copies in
-// flight and returns.
+// flight and returns.  The detector variant (DET), the last pass of a
+// multislice run, loads tiles the same way, squares the forward transform and
+// sums it into the rings instead of storing anything.
 // ---------------------------------------------------------------------------
 #ifndef STEM_COL_TMA_MINB_1024
 #define STEM_COL_TMA_MINB_1024 2
@@ -525,13 +527,14 @@ template <int N_> struct ColTmaCfg {
   static constexpr size_t XBUF = (size_t)(N + N / E) * C * sizeof(float2);
   static constexpr size_t TW = (size_t)TwLayout<N>::TOTAL * sizeof(float2);
   static constexpr size_t SMEM = 1024 + 2 * (size_t)STAGE_BYTES + XBUF + TW + 64;
+  static constexpr size_t SMEM_DET = SMEM + (size_t)kMaxRings * sizeof(float);   // + the tile's rings
   static constexpr int MB = N / 3;
   static constexpr int LO = (MB + 1 + C - 1) / C, HI0 = (N - MB) / C;
   static constexpr int BAND_TILES = LO + N / C - HI0;
   __device__ static int band_tile(int k) { return k >= LO ? k - LO + HI0 : k; }
 };
 
-template <int N_>
+template <int N_, bool DET>
 __global__ void __launch_bounds__(ColTmaCfg<N_>::THREADS, ColTmaCfg<N_>::MINB)
     k_col_slice_tma(const PassArgs a, const __grid_constant__ CUtensorMap map, int n_tiles) {
   using Cfg = ColTmaCfg<N_>;
@@ -542,6 +545,7 @@ __global__ void __launch_bounds__(ColTmaCfg<N_>::THREADS, ColTmaCfg<N_>::MINB)
   float2* xbuf = reinterpret_cast<float2*>(base + 2 * (size_t)Cfg::STAGE_BYTES);
   float2* tw = reinterpret_cast<float2*>(reinterpret_cast<unsigned char*>(xbuf) + Cfg::XBUF);
   uint64_t* bars = reinterpret_cast<uint64_t*>(reinterpret_cast<unsigned char*>(tw) + Cfg::TW);
+  float* ring_acc = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(bars) + 64);   // DET only
   const int tid = threadIdx.x;
   const int c = tid % C, t = tid / C;
   const SmemView<E, C> view{xbuf + c};
@@ -587,6 +591,42 @@ __global__ void __launch_bounds__(ColTmaCfg<N_>::THREADS, ColTmaCfg<N_>::MINB)
     const int wave = tile / Cfg::BAND_TILES;
     const int col0 = Cfg::band_tile(tile % Cfg::BAND_TILES) * C;
     const int col = col0 + c;
+    if constexpr (DET) {
+      // detector pass: nothing is stored back, so the buffer takes the tile
+      // after next as soon as every thread holds its values; the rings of the
+      // previous tile have been flushed, so they can be cleared
+      __syncthreads();
+      if (tid == 0 && tile + 2 * gridDim.x < n_tiles) issue(tile + 2 * gridDim.x, b);
+      for (int i = tid; i < a.n_rings; i += Cfg::THREADS) ring_acc[i] = 0.0f;
+      fft_dist<N, false>(v, view, t, sync, tw);
+      // |Psi_hat|^2 and ring of each pixel, column by column in row order (row
+      // stride S keeps the scattered writes free of bank conflicts); each warp
+      // then sums runs of 32 consecutive rows of one column (warp_run_add)
+      constexpr int S = N + 16 / C;
+      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < E; ++q) {
+        const int ky = t + q * T;
+        const int r = __ldg(a.lut + (size_t)ky * N + col) & kLutNoRing;
+        xbuf[c * S + ky] = make_float2(cabs2(v[q]), __int_as_float(r));
+      }
+      __syncthreads();
+      constexpr int NW = Cfg::THREADS / 32;
+      const int lane = tid & 31, warp = tid >> 5;
+#pragma unroll 4
+      for (int i = 0; i < E; ++i) {
+        const int idx = (warp + NW * i) * 32 + lane;
+        const float2 e = xbuf[(idx / N) * S + idx % N];
+        warp_run_add(ring_acc, __float_as_int(e.y), e.x, kLutNoRing);
+      }
+      __syncthreads();
+      float* out = a.rings + (size_t)wave * a.n_rings;
+      for (int i = tid; i < a.n_rings; i += Cfg::THREADS) {
+        const float acc = ring_acc[i];
+        if (acc != 0.0f) atomicAdd(out + i, acc * a.ring_scale);
+      }
+      continue;
+    }
     fft_dist<N, false>(v, view, t, sync, tw);
     const int m = signed_freq(col, N);
     const float2 px = cscale(__ldg(a.prop_x + col), a.prop_scale);
@@ -613,7 +653,7 @@ __global__ void __launch_bounds__(ColTmaCfg<N_>::THREADS, ColTmaCfg<N_>::MINB)
       }
     }
   }
-  if (tid == 0) bulk_wait_all();
+  if (!DET && tid == 0) bulk_wait_all();
 
   if (aborted && tid == 0) {
     if (a.status) atomicExch(a.status, (int)STEM_ERR_TIMEOUT);
@@ -751,18 +791,30 @@ static cudaError_t wave_tensor_map(const PassArgs& a, CUtensorMap* map) {
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-template <int N>
+template <int N, bool DET>
 static cudaError_t col_slice_tma(const PassArgs& a, cudaStream_t s) {
   using Cfg = ColTmaCfg<N>;
   static std::once_flag flag, occ_flag;
   static int occ = 0;
-  cudaError_t e = set_smem(k_col_slice_tma<N>, Cfg::SMEM, flag);
+  cudaError_t e = set_smem(k_col_slice_tma<N, DET>, DET ? Cfg::SMEM_DET : Cfg::SMEM, flag);
   if (e != cudaSuccess) return e;
   CUtensorMap map;
   if ((e = wave_tensor_map<N>(a, &map)) != cudaSuccess) return e;
   const int n_tiles = a.batch * Cfg::BAND_TILES;
-  const int grid = std::min(n_tiles, resident_ctas(k_col_slice_tma<N>, Cfg::THREADS, Cfg::SMEM, occ_flag, occ));
-  note_launch(), k_col_slice_tma<N><<<grid, Cfg::THREADS, Cfg::SMEM, s>>>(a, map, n_tiles);
+  int grid;
+  size_t smem = Cfg::SMEM;
+  if constexpr (DET) {
+    // the detector variant holds only this plan's rings, so that more CTAs fit
+    smem += ((size_t)a.n_rings * sizeof(float) + 15) / 16 * 16;
+    int dev = 0, sms = 148, per = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_col_slice_tma<N, DET>, Cfg::THREADS, smem);
+    grid = std::min(n_tiles, sms * std::max(per, 1));
+  } else {
+    grid = std::min(n_tiles, resident_ctas(k_col_slice_tma<N, DET>, Cfg::THREADS, smem, occ_flag, occ));
+  }
+  note_launch(), k_col_slice_tma<N, DET><<<grid, Cfg::THREADS, smem, s>>>(a, map, n_tiles);
   return cudaGetLastError();
 }
 
@@ -771,6 +823,11 @@ static cudaError_t col_slice_tma(const PassArgs& a, cudaStream_t s) {
 // it reads PRISM windows or other full fields.
 template <int N>
 static cudaError_t col_dispatch(int mode, const PassArgs& a, cudaStream_t s) {
+#if STEM_COL_TMA
+  // the detector pass that ends a slice loop reads only in-band column tiles
+  if constexpr (N == 2048 || N == 1024)
+    if (mode == COL_DET && a.band) return col_slice_tma<N, true>(a, s);
+#endif
   switch (mode) {
     case COL_DET: return a.band ? col_launch<N, COL_DET, true>(a, s) : col_launch<N, COL_DET, false>(a, s);
     case COL_DP: return a.band ? col_launch<N, COL_DP, true>(a, s) : col_launch<N, COL_DP, false>(a, s);
@@ -780,11 +837,11 @@ static cudaError_t col_dispatch(int mode, const PassArgs& a, cudaStream_t s) {
   }
 #if STEM_COL_TMA
   if constexpr (N == 2048)
-    if (mode == COL_SLICE) return col_slice_tma<2048>(a, s);
+    if (mode == COL_SLICE) return col_slice_tma<2048, false>(a, s);
 #endif
 #if STEM_COL_TMA_1024
   if constexpr (N == 1024)
-    if (mode == COL_SLICE) return col_slice_tma<1024>(a, s);
+    if (mode == COL_SLICE) return col_slice_tma<1024, false>(a, s);
 #endif
   if constexpr (N >= 64) {
     switch (mode) {

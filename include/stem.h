@@ -255,6 +255,19 @@ stem_status stem_prism_smatrix(stem_plan plan, const void* trans, int32_t f, ste
                                int32_t batch, void* smatrix, size_t smatrix_bytes,
                                void* workspace, size_t workspace_bytes, void* stream);
 
+/* Beams [b_begin, b_end) only (0 <= b_begin <= b_end <= n_beams), for an
+ * S-matrix whose beams are built on several devices ("PRISM Probe
+ * Simulations": every plane wave is propagated independently).  Writes those
+ * beams' values and scales, and the padding beams when b_end == n_beams;
+ * nothing else in the buffer is touched.  With the buffer zeroed beforehand on
+ * every device, summing the buffers of devices that built disjoint ranges
+ * covering [0, n_beams) gives exactly the whole S-matrix (each sum adds only
+ * zeros), which is how an all-reduce assembles it.  Otherwise as
+ * stem_prism_smatrix; STEM_ERR_INVALID for a range outside [0, n_beams]. */
+stem_status stem_prism_smatrix_range(stem_plan plan, const void* trans, int32_t f, stem_storage storage,
+                                     int32_t batch, int32_t b_begin, int32_t b_end, void* smatrix,
+                                     size_t smatrix_bytes, void* workspace, size_t workspace_bytes, void* stream);
+
 /* The S-matrix built under the streaming memory model: trans_host as for
  * stem_multislice_scan_streamed (host stack, copied slice by slice into 3
  * device buffers; every batch of beams copies all slices); workspace >=

@@ -70,6 +70,8 @@ SIGNATURES = {
     "stem_prism_smatrix_workspace": (c_size_t, [c_void_p, c_int32]),
     "stem_prism_smatrix": (c_int32, [c_void_p, c_void_p, c_int32, c_int32, c_int32, c_void_p, c_size_t,
                                      c_void_p, c_size_t, c_void_p]),
+    "stem_prism_smatrix_range": (c_int32, [c_void_p, c_void_p, c_int32, c_int32, c_int32, c_int32, c_int32,
+                                           c_void_p, c_size_t, c_void_p, c_size_t, c_void_p]),
     "stem_prism_output_workspace": (c_size_t, [c_void_p, c_int32, c_int32]),
     "stem_prism_output": (c_int32, [c_void_p, c_int32, c_int32, c_int32, c_void_p, c_void_p, c_int64, c_int32,
                                     c_float, c_void_p, c_void_p, c_size_t, c_void_p]),

@@ -261,7 +261,11 @@ class Plan:
         return out
 
     def prism_smatrix(self, trans: torch.Tensor, f: int, storage: str = "f32", batch: int = 128,
-                      workspace: Optional[torch.Tensor] = None, out: Optional[torch.Tensor] = None) -> SMatrix:
+                      workspace: Optional[torch.Tensor] = None, out: Optional[torch.Tensor] = None,
+                      beams: Optional[Tuple[int, int]] = None) -> SMatrix:
+        """The compact S-matrix; with beams=(b0, b1) only beams [b0, b1) are
+        built into a zeroed buffer (a buffer passed as `out` must be zeroed by
+        the caller), so that buffers of disjoint ranges sum to the whole."""
         lib = _lib.load()
         trans = _need(trans, torch.complex64, "trans", (self.n_slices, self.n, self.n))
         st = STORAGE[storage]
@@ -270,11 +274,27 @@ class Plan:
             raise ValueError(f"unsupported f={f} or storage={storage}")
         nb = len(self.prism_beams(f))
         batch = int(max(1, min(batch, nb)))
-        buf = out if out is not None else torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        alloc = torch.zeros if beams is not None else torch.empty
+        buf = out if out is not None else alloc(nbytes, dtype=torch.uint8, device=self.device)
         ws = workspace if workspace is not None else _workspace(
             lib.stem_prism_smatrix_workspace(self._h, batch), self.device)
-        check(lib.stem_prism_smatrix(self._h, _ptr(trans), f, st, batch, _ptr(buf), buf.numel(), _ptr(ws),
-                                     ws.numel(), _stream(self.device)), "stem_prism_smatrix")
+        if beams is None:
+            check(lib.stem_prism_smatrix(self._h, _ptr(trans), f, st, batch, _ptr(buf), buf.numel(), _ptr(ws),
+                                         ws.numel(), _stream(self.device)), "stem_prism_smatrix")
+        else:
+            check(lib.stem_prism_smatrix_range(self._h, _ptr(trans), f, st, batch, int(beams[0]), int(beams[1]),
+                                               _ptr(buf), buf.numel(), _ptr(ws), ws.numel(), _stream(self.device)),
+                  "stem_prism_smatrix_range")
+        nbp = (nb + 63) // 64 * 64
+        return SMatrix(buf, f, storage, nb, nbp, (nbp * 4 + 255) // 256 * 256, self.n)
+
+    def prism_smatrix_view(self, buf: torch.Tensor, f: int, storage: str) -> SMatrix:
+        """An S-matrix handle on an existing buffer (e.g. one assembled from
+        beam ranges built on several devices)."""
+        lib = _lib.load()
+        if buf.numel() < lib.stem_prism_smatrix_bytes(self._h, f, STORAGE[storage]):
+            raise ValueError("buffer smaller than the S-matrix")
+        nb = len(self.prism_beams(f))
         nbp = (nb + 63) // 64 * 64
         return SMatrix(buf, f, storage, nb, nbp, (nbp * 4 + 255) // 256 * 256, self.n)
 

@@ -494,9 +494,10 @@ size_t stem_prism_smatrix_streamed_workspace(stem_plan pl, int32_t batch) {
          (size_t)kStreamBufs * pl->n * pl->n * sizeof(float2);
 }
 
+// Beams [b_begin, b_end) of the S-matrix (b_end < 0: to the last beam).
 static stem_status run_smatrix(stem_plan pl, const void* trans, bool streamed, int32_t f, stem_storage storage,
                                int32_t batch, void* smatrix, size_t smatrix_bytes, void* ws, size_t ws_bytes,
-                               void* stream) {
+                               void* stream, int32_t b_begin = 0, int32_t b_end = -1) {
   if (!pl || !trans || !smatrix || !ws || !f_ok(pl, f) || storage < STEM_F32 || storage > STEM_BF16 || batch < 1 ||
       batch > 65535)
     return STEM_ERR_INVALID;
@@ -504,6 +505,8 @@ static stem_status run_smatrix(stem_plan pl, const void* trans, bool streamed, i
   if (n < 64) return STEM_ERR_UNSUPPORTED;
   const int lf = log2i(f);
   const int nb = pl->n_beams[lf];
+  if (b_end < 0) b_end = nb;
+  if (b_begin < 0 || b_begin > b_end || b_end > nb) return STEM_ERR_INVALID;
   const SmatLayout L = smatrix_layout(n, nb, storage);
   const size_t need = streamed ? stem_prism_smatrix_streamed_workspace(pl, batch) : stem_prism_smatrix_workspace(pl, batch);
   if (smatrix_bytes < L.total || ws_bytes < need) return STEM_ERR_NOMEM;
@@ -524,8 +527,8 @@ static stem_status run_smatrix(stem_plan pl, const void* trans, bool streamed, i
   a.prop_scale = 1.0f / (float)plane;
   a.beam_max = reinterpret_cast<unsigned*>(static_cast<char*>(ws) + smatrix_ws_waves(n, batch));
   a.status = pl->status;
-  for (int b0 = 0; b0 < nb; b0 += batch) {
-    a.batch = std::min(batch, nb - b0);
+  for (int b0 = b_begin; b0 < b_end; b0 += batch) {
+    a.batch = std::min(batch, b_end - b0);
     a.beams = pl->beams[lf] + b0;
     cudaError_t e = cudaMemsetAsync(a.beam_max, 0, a.batch * sizeof(unsigned), s);
     for (int sl = 0; sl < pl->p.n_slices && e == cudaSuccess; ++sl) {
@@ -544,6 +547,14 @@ static stem_status run_smatrix(stem_plan pl, const void* trans, bool streamed, i
 stem_status stem_prism_smatrix(stem_plan pl, const void* trans, int32_t f, stem_storage storage, int32_t batch,
                                void* smatrix, size_t smatrix_bytes, void* ws, size_t ws_bytes, void* stream) {
   return run_smatrix(pl, trans, false, f, storage, batch, smatrix, smatrix_bytes, ws, ws_bytes, stream);
+}
+
+stem_status stem_prism_smatrix_range(stem_plan pl, const void* trans, int32_t f, stem_storage storage, int32_t batch,
+                                     int32_t b_begin, int32_t b_end, void* smatrix, size_t smatrix_bytes, void* ws,
+                                     size_t ws_bytes, void* stream) {
+  if (b_end < 0) return STEM_ERR_INVALID;
+  return run_smatrix(pl, trans, false, f, storage, batch, smatrix, smatrix_bytes, ws, ws_bytes, stream, b_begin,
+                     b_end);
 }
 
 stem_status stem_prism_smatrix_streamed(stem_plan pl, const void* trans_host, int32_t f, stem_storage storage,

@@ -424,3 +424,26 @@ def test_probe_phase_far_from_the_origin(api):
     near_pr = plan.prism_output(sm, dev(xy), chunk=4).cpu().numpy()
     far_pr = plan.prism_output(sm, dev(far), chunk=4).cpu().numpy()
     assert np.allclose(far_pr, near_pr, rtol=1e-5, atol=1e-9 * near_pr.max())
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+def test_prism_smatrix_beam_ranges_sum_to_the_whole(api, storage):
+    """Beams built in disjoint ranges into zeroed buffers (as ranks of the PRISM
+    split do) sum, value by value in the stored type, to exactly the S-matrix
+    built in one call; the last range also writes the padding beams."""
+    w, xyz, gauss = _small_prism_case(n=128, f=2)
+    plan = api.Plan.from_workload(w)
+    p, tref = _oracle_trans(w, xyz, gauss)
+    t = dev(tref, torch.complex64)
+    whole = plan.prism_smatrix(t, 2, storage, batch=16)
+    nb = whole.n_beams
+    cuts = [0, 5, 5, nb // 2, nb]                  # includes an empty range
+    parts = [plan.prism_smatrix(t, 2, storage, batch=16, beams=(a, b)) for a, b in zip(cuts[:-1], cuts[1:])]
+    scales = sum(s.scales() for s in parts)
+    data = sum(s.data().float() for s in parts).to(whole.data().dtype)
+    assert torch.equal(scales, whole.scales())
+    assert torch.equal(data, whole.data())
+    # a range outside [0, n_beams] is refused
+    from paper_1706_08563_b300 import _lib
+    with pytest.raises(_lib.StemError):
+        plan.prism_smatrix(t, 2, storage, beams=(3, nb + 1))

@@ -68,6 +68,61 @@ def _worker(rank, world, port, out_path):
         dist.destroy_process_group()
 
 
+def _prism_case():
+    import workloads as W
+    from oracle import stem as O
+    w = W.Workload("gp", (10.0, 12.0, 4.0), 14, 32, 2, 2.0, 200.0, 30.0, 3, 4.0, 20, f=(2,))
+    p = O.params_from(w)
+    xyz, gauss = W.atoms(w, seed=8)
+    xy = W.random_positions(w, 7, seed=9)
+    return w, p, xyz, gauss, xy
+
+
+def _prism_worker(rank, world, port, out_path):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        from oracle import stem as O
+        from paper_1706_08563_b300.parallel import sharded_prism
+        w, p, xyz, gauss, xy = _prism_case()
+        t = O.transmission(p, O.projected_potential(p, xyz, gauss))
+        beams = O.prism_beams(p, 2)
+        smat = torch.zeros((len(beams), p.n, p.n, 2), dtype=torch.float64)
+        built = []
+
+        def build(b0, b1):
+            built.append((b0, b1))
+            s = O.prism_smatrix(p, t, beams[b0:b1])
+            smat[b0:b1] = torch.from_numpy(np.stack([s.real, s.imag], axis=-1))
+
+        def output(a, b):
+            s = smat[..., 0].numpy() + 1j * smat[..., 1].numpy()
+            return torch.from_numpy(O.prism_rings(p, s, beams, 2, xy[a:b]))
+        rings = sharded_prism(len(beams), len(xy), build, [smat], output)
+        assert built[0][1] - built[0][0] < len(beams)          # each rank built only part of the beams
+        if rank == 0:
+            np.savez(out_path, rings=rings.numpy(), smat=smat.numpy())
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_prism_split_match_one_process(repo_tmp):
+    """PRISM split over two ranks: beams sharded for the S-matrix and summed
+    into every rank's copy, then probes sharded for the output step; the rings
+    and the assembled S-matrix equal one process doing it all."""
+    from oracle import stem as O
+    out = os.path.join(repo_tmp, "p.npz")
+    mp.spawn(_prism_worker, args=(2, _free_port(), out), nprocs=2, join=True)
+    got = np.load(out)
+    w, p, xyz, gauss, xy = _prism_case()
+    t = O.transmission(p, O.projected_potential(p, xyz, gauss))
+    beams = O.prism_beams(p, 2)
+    s = O.prism_smatrix(p, t, beams)
+    assert np.array_equal(got["smat"][..., 0] + 1j * got["smat"][..., 1], s)
+    assert np.allclose(got["rings"], O.prism_rings(p, s, beams, 2, xy), rtol=0, atol=1e-15)
+
+
 def test_two_gloo_ranks_match_one_process(repo_tmp):
     import workloads as W
     from oracle import stem as O

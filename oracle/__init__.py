@@ -17,7 +17,11 @@ wavelengths, a Jacobi-Anger closed form for a phase grating followed by Fresnel
 propagation, a Gaussian-beam Fresnel closed form, V=0 closed forms for
 multislice and PRISM rings, PRISM f=1 == multislice, norm bookkeeping
 (Parseval), linearity, cyclic-shift covariance, analytic single-atom
-potentials and the Gaussian sum rule.
+potentials and the Gaussian sum rule; PRISM shift covariance in a cell with
+Lx != Ly (fixes the window crop's axes); the Fourier-cropped S-matrix against
+an explicit trigonometric sum over the band, its zero-padded inverse, f = 1
+against multislice, the free-space closed form and shift covariance on the
+cropped grid.
 
 Parity unpinned: PRISM with f > 1 against multislice (the paper only calls
 the f=4 result "almost indistinguishable"); the oracle runs the same

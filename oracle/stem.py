@@ -135,11 +135,12 @@ def ring_table(p: Params, edges: Optional[Sequence[float]] = None) -> np.ndarray
     return r
 
 
-def coarse_ring_table(p: Params, f: int, edges: Optional[Sequence[float]] = None) -> np.ndarray:
-    """Ring table of a W x W window FFT, W = N/f: coarse frequency (nu, mu) is the
-    fine frequency (f nu, f mu), so the table is the fine one sampled every f-th
-    signed index."""
-    w = p.n // f
+def coarse_ring_table(p: Params, f: int, edges: Optional[Sequence[float]] = None,
+                      w: Optional[int] = None) -> np.ndarray:
+    """Ring table of a W x W window FFT (W = N/f unless given): the window spans
+    L/f, so coarse frequency (nu, mu) is the fine frequency (f nu, f mu) and the
+    table is the fine one sampled every f-th signed index."""
+    w = p.n // f if w is None else w
     fine = ring_table(p, edges)
     mu = freq_index(w)
     idx = np.mod(f * mu, p.n)
@@ -312,16 +313,42 @@ def prism_smatrix(p: Params, trans: np.ndarray, beams: np.ndarray, chunk: int = 
     return out
 
 
-def prism_window_origin(p: Params, f: int, xy: np.ndarray) -> np.ndarray:
-    """Window origin per probe (int64 [P, 2] of (ox, oy)): the pixel nearest the probe
-    (round half up) minus W/2, wrapped modulo N."""
-    w = p.n // f
-    dx = p.cell[0] / p.n
-    dy = p.cell[1] / p.n
+def cropped_grid(n: int) -> int:
+    """Side of the Fourier-cropped S-matrix grid: 3 N / 4, the size 3 * 2^k just
+    above the 2/3 band (2 floor(N/3) + 1 frequencies per axis)."""
+    return 3 * n // 4
+
+
+def prism_smatrix_cropped(p: Params, trans: np.ndarray, beams: np.ndarray, chunk: int = 16) -> np.ndarray:
+    """Fourier-cropped compact S-matrix ("Description of Algorithms": the output
+    probe is a Fourier interpolation of the plane waves).  Each exit wave is
+    band-limited (9 (m^2 + n^2) <= N^2), so its spectrum fits on the grid of
+    signed frequencies |m|, |n| < N'/2, N' = 3 N / 4; the inverse transform
+    there samples the same band-limited wave at the N' x N' points
+    (j Lx / N', i Ly / N'): S'_b = (1 / N^2) sum_k Psi_hat_b(k) e^{2 pi i k.r}.
+    Returns [n_b, N', N'] complex128."""
+    n2 = cropped_grid(p.n)
+    idx = np.mod(freq_index(n2), p.n)          # positions of the N' signed frequencies in N-point order
+    out = np.empty((beams.shape[0], n2, n2), dtype=np.complex128)
+    for c0 in range(0, beams.shape[0], chunk):
+        psi = plane_waves(p, beams[c0:c0 + chunk])
+        spec = multislice_k(p, trans, psi)[:, idx][:, :, idx]
+        out[c0:c0 + chunk] = np.fft.ifft2(spec, axes=(-2, -1)) * (float(n2) / p.n) ** 2
+    return out
+
+
+def prism_window_origin(p: Params, f: int, xy: np.ndarray, grid: Optional[int] = None) -> np.ndarray:
+    """Window origin per probe (int64 [P, 2] of (ox, oy)) on a grid of `grid`
+    pixels per side (the simulation grid N unless given): the pixel nearest the
+    probe (round half up) minus W/2, W = grid / f, wrapped modulo grid."""
+    n = p.n if grid is None else grid
+    w = n // f
+    dx = p.cell[0] / n
+    dy = p.cell[1] / n
     xy = np.atleast_2d(np.asarray(xy, dtype=np.float64))
     ox = np.floor(xy[:, 0] / dx + 0.5).astype(np.int64) - w // 2
     oy = np.floor(xy[:, 1] / dy + 0.5).astype(np.int64) - w // 2
-    return np.stack([np.mod(ox, p.n), np.mod(oy, p.n)], axis=1)
+    return np.stack([np.mod(ox, n), np.mod(oy, n)], axis=1)
 
 
 def prism_coefficients(p: Params, beams: np.ndarray, xy: np.ndarray) -> np.ndarray:
@@ -344,39 +371,50 @@ def _smatrix_crop(smatrix, rows: np.ndarray, cols: np.ndarray) -> np.ndarray:
 
 
 def prism_window_waves(p: Params, smatrix, beams: np.ndarray, f: int,
-                       xy: np.ndarray) -> np.ndarray:
-    """Psi_p(v, u) = sum_b c[p, b] S_b((o_p + (u, v)) mod N), [P, W, W] (rows v, cols u)."""
-    w = p.n // f
-    org = prism_window_origin(p, f, xy)
+                       xy: np.ndarray, grid: Optional[int] = None) -> np.ndarray:
+    """Psi_p(v, u) = sum_b c[p, b] S_b((o_p + (u, v)) mod n), [P, W, W] (rows v, cols u),
+    for an S-matrix on a grid of n = `grid` pixels per side (N unless given), W = n / f."""
+    n = p.n if grid is None else grid
+    w = n // f
+    org = prism_window_origin(p, f, xy) if grid is None else prism_window_origin(p, f, xy, grid)
     coef = prism_coefficients(p, beams, xy)
     out = np.empty((org.shape[0], w, w), dtype=np.complex128)
     u = np.arange(w)
     for i in range(org.shape[0]):
-        rows = np.mod(org[i, 1] + u, p.n)
-        cols = np.mod(org[i, 0] + u, p.n)
+        rows = np.mod(org[i, 1] + u, n)
+        cols = np.mod(org[i, 0] + u, n)
         crop = _smatrix_crop(smatrix, rows, cols)            # [n_b, W, W]
         out[i] = np.tensordot(coef[i], crop, axes=(0, 0))
     return out
 
 
-def prism_dp(p: Params, smatrix, beams: np.ndarray, f: int, xy: np.ndarray) -> np.ndarray:
+def prism_dp(p: Params, smatrix, beams: np.ndarray, f: int, xy: np.ndarray,
+             grid: Optional[int] = None) -> np.ndarray:
     """PRISM 4D output on the window grid: |FFT_W(Psi_p)|^2 / W^4 inside the band
-    limit (coarse (mu, nu) standing for (f mu, f nu)), [P, W, W] in FFT order."""
-    w = p.n // f
-    spec = np.fft.fft2(prism_window_waves(p, smatrix, beams, f, xy), axes=(-2, -1))
-    return np.abs(spec) ** 2 / float(w) ** 4 * bandlimit_mask(w)[None]
+    limit (coarse (mu, nu) standing for (f mu, f nu), so the limit is
+    9 (f mu)^2 + 9 (f nu)^2 <= N^2), [P, W, W] in FFT order, W = grid / f."""
+    n = p.n if grid is None else grid
+    w = n // f
+    args = () if grid is None else (grid,)
+    spec = np.fft.fft2(prism_window_waves(p, smatrix, beams, f, xy, *args), axes=(-2, -1))
+    mu = freq_index(w)
+    mask = 9 * f * f * (mu[None, :] ** 2 + mu[:, None] ** 2) <= p.n * p.n
+    return np.abs(spec) ** 2 / float(w) ** 4 * mask[None]
 
 
 def prism_rings(p: Params, smatrix, beams: np.ndarray, f: int,
-                xy: np.ndarray, chunk: int = 64) -> np.ndarray:
+                xy: np.ndarray, chunk: int = 64, grid: Optional[int] = None) -> np.ndarray:
     """PRISM annular-ring output [P, n_rings]: window beam sum, W x W FFT, |.|^2 / W^4,
-    binned on the coarse grid."""
-    w = p.n // f
-    table = coarse_ring_table(p, f)
+    binned on the coarse grid (S-matrix on a grid of `grid` pixels per side, N
+    unless given; W = grid / f)."""
+    n = p.n if grid is None else grid
+    w = n // f
+    table = coarse_ring_table(p, f, w=w)
     xy = np.atleast_2d(np.asarray(xy, dtype=np.float64))
     out = np.zeros((xy.shape[0], p.n_rings))
+    args = () if grid is None else (grid,)
     for c0 in range(0, xy.shape[0], chunk):
-        win = prism_window_waves(p, smatrix, beams, f, xy[c0:c0 + chunk])
+        win = prism_window_waves(p, smatrix, beams, f, xy[c0:c0 + chunk], *args)
         spec = np.fft.fft2(win, axes=(-2, -1))
         out[c0:c0 + chunk] = detector_rings(table, p.n_rings, np.abs(spec) ** 2) / float(w) ** 4
     return out

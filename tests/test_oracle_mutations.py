@@ -55,12 +55,13 @@ def _probe_unnormalised(p, xy):
     return O._orig_probe_k(p, xy) * math.sqrt(int(O.aperture(p).sum()))
 
 
-def _origin_round_down(p, f, xy):
-    w = p.n // f
+def _origin_round_down(p, f, xy, grid=None):
+    n = p.n if grid is None else grid
+    w = n // f
     xy = np.atleast_2d(xy)
-    ox = np.floor(xy[:, 0] / p.dx).astype(np.int64) - w // 2
-    oy = np.floor(xy[:, 1] / p.dy).astype(np.int64) - w // 2
-    return np.stack([np.mod(ox, p.n), np.mod(oy, p.n)], axis=1)
+    ox = np.floor(xy[:, 0] / (p.cell[0] / n)).astype(np.int64) - w // 2
+    oy = np.floor(xy[:, 1] / (p.cell[1] / n)).astype(np.int64) - w // 2
+    return np.stack([np.mod(ox, n), np.mod(oy, n)], axis=1)
 
 
 def _coef_conj(p, beams, xy):
@@ -101,7 +102,7 @@ def _chi_cs_no_lambda_cubed(p, kx, ky):
     return math.pi * p.lam * p.defocus * k2 + 0.5 * math.pi * p.cs * p.lam * k2 * k2
 
 
-def _window_crop_axes_swapped(p, smatrix, beams, f, xy):
+def _window_crop_axes_swapped(p, smatrix, beams, f, xy, grid=None):
     # the window's rows taken from the x origin and its columns from the y origin
     w = p.n // f
     org = O.prism_window_origin(p, f, xy)
@@ -113,6 +114,19 @@ def _window_crop_axes_swapped(p, smatrix, beams, f, xy):
         cols = np.mod(org[i, 1] + u, p.n)
         out[i] = np.tensordot(coef[i], O._smatrix_crop(smatrix, rows, cols), axes=(0, 0))
     return out
+
+
+def _cropped_unnormalised(p, trans, beams, chunk=16):
+    # the inverse transform's 1/N'^2 left in place of 1/N^2
+    return O._orig_prism_smatrix_cropped(p, trans, beams, chunk) * (p.n / float(O.cropped_grid(p.n))) ** 2
+
+
+def _cropped_first_indices(p, trans, beams, chunk=16):
+    # the first N' FFT indices kept instead of the N' signed frequencies
+    n2 = O.cropped_grid(p.n)
+    psi = O.plane_waves(p, beams)
+    spec = O.multislice_k(p, trans, psi)[:, :n2, :n2]
+    return np.fft.ifft2(spec, axes=(-2, -1)) * (float(n2) / p.n) ** 2
 
 
 def _fp_first_config_only(p, configs, gauss, xy, algo="ms", f=1):
@@ -138,6 +152,10 @@ CASES = [
      [lambda: pins.test_prism_shift_covariance_non_square_cell(2),
       lambda: pins.test_prism_shift_covariance_non_square_cell(4)]),
     ("slice_index", _slice_round, [pins.test_slice_assignment]),
+    ("prism_smatrix_cropped", _cropped_unnormalised, [pins.test_cropped_smatrix_samples_the_band_limited_wave,
+                                                      pins.test_prism_cropped_f1_equals_multislice]),
+    ("prism_smatrix_cropped", _cropped_first_indices, [pins.test_cropped_smatrix_samples_the_band_limited_wave,
+                                                       pins.test_prism_cropped_f1_equals_multislice]),
     ("projected_potential", _potential_one_gaussian, [pins.test_potential_sum_rule_and_peak]),
     ("wavelength", _lambda_nonrel, [pins.test_wavelength_textbook_values]),
     ("multislice_k", _ms_last_slice_unpropagated, [pins.test_phase_grating_one_slice_jacobi_anger]),

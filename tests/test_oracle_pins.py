@@ -506,3 +506,95 @@ def test_propagator_semigroup():
     a = O.multislice_k(half, np.ones((2, p.n, p.n), complex), psi)
     b = O.multislice_k(full, np.ones((1, p.n, p.n), complex), psi)
     assert np.allclose(a, b, atol=1e-12)
+
+
+# ------------------------------------------------- Fourier-cropped S-matrix
+def test_cropped_smatrix_samples_the_band_limited_wave():
+    """S'_b on the cropped grid N' = 3N/4 is the band-limited exit wave S_b
+    evaluated at the points (j Lx / N', i Ly / N'): checked against an explicit
+    trigonometric sum over the band (Lx != Ly), and zero-padding its spectrum
+    back to N reproduces S_b on the simulation grid."""
+    p = O.Params((5.0, 6.0, 4.0), 16, 2, 2.0, 200.0, 60.0, 4.0, 40)
+    n, n2 = 16, O.cropped_grid(16)
+    assert n2 == 12
+    t = _random_trans(p, seed=11, vmax=40.0)
+    beams = O.prism_beams(p, 1)[::3]
+    full = O.prism_smatrix(p, t, beams)
+    crop = O.prism_smatrix_cropped(p, t, beams)
+    assert crop.shape == (len(beams), n2, n2)
+    band = [(m, k) for m in range(-n // 2, n // 2) for k in range(-n // 2, n // 2) if 9 * (m * m + k * k) <= n * n]
+    jj = np.arange(n2)
+    for b in range(len(beams)):
+        spec = np.fft.fft2(full[b])
+        want = np.zeros((n2, n2), complex)
+        for (m, k) in band:
+            want += spec[k % n, m % n] * np.exp(2j * math.pi * (m * jj[None, :] + k * jj[:, None]) / n2)
+        want /= n * n
+        assert np.max(np.abs(crop[b] - want)) < 1e-12 * np.max(np.abs(want))
+        # zero-padded back to N: the band-limited wave itself
+        sc = np.fft.fft2(crop[b]) * (n / n2) ** 2
+        pad = np.zeros((n, n), complex)
+        f2 = O.freq_index(n2)
+        pad[np.ix_(np.mod(f2, n), np.mod(f2, n))] = sc
+        assert np.max(np.abs(np.fft.ifft2(pad) - full[b])) < 1e-12 * np.max(np.abs(full[b]))
+
+
+def test_prism_cropped_f1_equals_multislice():
+    """With f = 1 the window is the whole cropped cell and its FFT holds the
+    multislice exit spectrum on every in-band frequency: the rings are those of
+    multislice."""
+    p = O.Params((8.0, 9.0, 6.0), 32, 3, 2.0, 200.0, 30.0, 4.0, 40)
+    rng = np.random.default_rng(12)
+    t = O.transmission(p, rng.random((3, 32, 32)) * 80.0)
+    xy = np.array([[0.3, 0.7], [4.4, 2.25], [7.9, 8.9]])
+    beams = O.prism_beams(p, 1)
+    s = O.prism_smatrix_cropped(p, t, beams)
+    pr = O.prism_rings(p, s, beams, 1, xy, grid=O.cropped_grid(p.n))
+    assert np.max(np.abs(pr - O.multislice_rings(p, t, xy))) < 1e-12
+
+
+@pytest.mark.parametrize("f", [2, 4])
+def test_prism_cropped_free_space_closed_form(f):
+    """V = 0: each cropped exit wave is a plane wave sampled on the N' grid, whose
+    window (W' = N'/f pixels over L/f) holds a whole number of its periods, so each
+    beam lands on one window-FFT pixel: ring i holds |beams in ring i| / n_b."""
+    p = O.Params((16.0, 16.0, 6.0), 64, 3, 2.0, 80.0, 30.0, 3.0, 40)
+    t = np.ones((3, 64, 64), complex)
+    beams = O.prism_beams(p, f)
+    s = O.prism_smatrix_cropped(p, t, beams)
+    xy = np.array([[1.0, 2.0], [9.3, 14.1]])
+    rings = O.prism_rings(p, s, beams, f, xy, grid=O.cropped_grid(64))
+    counts = np.zeros(p.n_rings)
+    for (m, n) in beams:
+        r = int(math.floor(p.lam * math.sqrt((m / 16.0) ** 2 + (n / 16.0) ** 2) * 1000.0 / 3.0))
+        if r < p.n_rings:
+            counts[r] += 1
+    for row in rings:
+        assert np.max(np.abs(row - counts / len(beams))) < 1e-12
+
+
+def test_prism_cropped_shift_covariance_non_square_cell():
+    """Atoms moved by (4, -8) pixels of the simulation grid = (3, -6) pixels of
+    the cropped grid (Lx != Ly) and probes moved by the same vector: the cropped
+    window waves are unchanged (fixes the crop orientation and the window origin
+    on the cropped grid)."""
+    p = O.Params((10.0, 13.0, 4.0), 32, 2, 2.0, 200.0, 30.0, 4.0, 40)
+    n2 = O.cropped_grid(p.n)
+    rng = np.random.default_rng(63)
+    xyz = rng.random((14, 3)) * np.array(p.cell)
+    gauss = np.tile(np.array([5.0, 0.2, 2.0, 0.6], np.float32), (14, 1))
+    shift = np.array([4 * p.dx, -8 * p.dy, 0.0])
+    xyz2 = xyz + shift
+    xyz2[:, 0] %= p.cell[0]
+    xyz2[:, 1] %= p.cell[1]
+    t1 = O.transmission(p, O.projected_potential(p, xyz, gauss))
+    t2 = O.transmission(p, O.projected_potential(p, xyz2, gauss))
+    beams = O.prism_beams(p, 2)
+    s1 = O.prism_smatrix_cropped(p, t1, beams)
+    s2 = O.prism_smatrix_cropped(p, t2, beams)
+    dxc, dyc = p.cell[0] / n2, p.cell[1] / n2
+    xy = np.array([[1.1 * dxc, 2.3 * dyc], [15.2 * dxc, 7.9 * dyc], [22.7 * dxc, 19.4 * dyc]])
+    w1 = O.prism_window_waves(p, s1, beams, 2, xy, n2)
+    w2 = O.prism_window_waves(p, s2, beams, 2, xy + shift[:2], n2)
+    assert np.max(np.abs(w1 - w2)) < 1e-10 * np.max(np.abs(w1))
+    assert np.max(np.abs(O.prism_window_waves(p, s2, beams, 2, xy, n2) - w1)) > 1e-5 * np.max(np.abs(w1))

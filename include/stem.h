@@ -59,7 +59,19 @@ typedef enum {
  * per-beam power-of-two scale s_b (its largest |Re| or |Im| rounded up to a
  * power of two); the beam sum multiplies the coefficient by s_b and accumulates
  * in FP32. */
-typedef enum { STEM_F32 = 0, STEM_F16 = 1, STEM_BF16 = 2 } stem_storage;
+typedef enum { STEM_F32 = 0, STEM_F16 = 1, STEM_BF16 = 2, STEM_CROPPED = 16 } stem_storage;
+/* STEM_CROPPED, OR-ed into the element type, selects the Fourier-cropped
+ * S-matrix ("Description of Algorithms": the PRISM output probe is a Fourier
+ * interpolation of the plane waves).  Every exit wave is band-limited by the
+ * 2/3 limit 9 (m^2 + n^2) <= N^2, so its spectrum fits on the grid of signed
+ * frequencies |m|, |n| < N'/2 with N' = 3N/4, and the inverse transform there
+ * samples the same wave at the N' x N' points (j Lx / N', i Ly / N'):
+ *   S'_b(r') = (1 / N^2) sum_{k in band} Psi_hat_b(k) exp(2 pi i k . r').
+ * The S-matrix is stored on that grid (9/16 of the bytes) and the output uses
+ * windows of W' = N' / f = 3W/4 pixels over the same L / f, their W' x W'
+ * transforms giving the same coarse frequencies (mu, nu) <-> (f mu, f nu).
+ * It needs n >= 64.  Every call that takes a storage code accepts the flag;
+ * an S-matrix must be read back with the code it was built with. */
 
 /* Beam-sum engine for stem_prism_output. */
 typedef enum {

@@ -21,6 +21,7 @@ STEM_ERR_UNSUPPORTED = -4
 STEM_ERR_TIMEOUT = -5
 
 STORAGE = {"f32": 0, "f16": 1, "bf16": 2}
+STEM_CROPPED = 16          # storage flag: Fourier-cropped S-matrix on the 3N/4 grid
 ENGINE = {"auto": 0, "simt": 1, "tensor": 2}
 
 

@@ -16,7 +16,7 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import ENGINE, STORAGE, StemParams, check
+from ._lib import ENGINE, STEM_CROPPED, STORAGE, StemParams, check
 
 
 def _stream(device: torch.device) -> ctypes.c_void_p:
@@ -62,7 +62,13 @@ class SMatrix:
     n_beams: int
     nbp: int
     data_offset: int
-    n: int
+    n: int                     # side of the grid it is stored on (N, or 3N/4 when cropped)
+    cropped: bool = False
+
+    @property
+    def code(self) -> int:
+        """The storage code of the C ABI (element type, with STEM_CROPPED when cropped)."""
+        return STORAGE[self.storage] | (STEM_CROPPED if self.cropped else 0)
 
     def scales(self) -> torch.Tensor:
         return self.buf[: 4 * self.nbp].view(torch.float32)
@@ -99,7 +105,8 @@ class SMatrix:
         mismatched plan.  ``tag`` names the specimen (the plan does not know
         the atoms); loading with a different tag is refused too."""
         meta = dict(version=SMATRIX_FILE_VERSION, f=self.f, storage=self.storage, n_beams=self.n_beams,
-                    nbp=self.nbp, data_offset=self.data_offset, n=self.n, plan=plan.smatrix_key(), tag=tag)
+                    nbp=self.nbp, data_offset=self.data_offset, n=self.n, cropped=self.cropped,
+                    plan=plan.smatrix_key(), tag=tag)
         np.savez(path, buf=self.buf.cpu().numpy(), meta=np.array(json.dumps(meta)))
 
 
@@ -262,13 +269,14 @@ class Plan:
 
     def prism_smatrix(self, trans: torch.Tensor, f: int, storage: str = "f32", batch: int = 128,
                       workspace: Optional[torch.Tensor] = None, out: Optional[torch.Tensor] = None,
-                      beams: Optional[Tuple[int, int]] = None) -> SMatrix:
+                      beams: Optional[Tuple[int, int]] = None, cropped: bool = False) -> SMatrix:
         """The compact S-matrix; with beams=(b0, b1) only beams [b0, b1) are
         built into a zeroed buffer (a buffer passed as `out` must be zeroed by
-        the caller), so that buffers of disjoint ranges sum to the whole."""
+        the caller), so that buffers of disjoint ranges sum to the whole.
+        cropped: store it Fourier-cropped on the 3N/4 grid."""
         lib = _lib.load()
         trans = _need(trans, torch.complex64, "trans", (self.n_slices, self.n, self.n))
-        st = STORAGE[storage]
+        st = STORAGE[storage] | (STEM_CROPPED if cropped else 0)
         nbytes = lib.stem_prism_smatrix_bytes(self._h, f, st)
         if nbytes == 0:
             raise ValueError(f"unsupported f={f} or storage={storage}")
@@ -286,17 +294,19 @@ class Plan:
                                                _ptr(buf), buf.numel(), _ptr(ws), ws.numel(), _stream(self.device)),
                   "stem_prism_smatrix_range")
         nbp = (nb + 63) // 64 * 64
-        return SMatrix(buf, f, storage, nb, nbp, (nbp * 4 + 255) // 256 * 256, self.n)
+        return SMatrix(buf, f, storage, nb, nbp, (nbp * 4 + 255) // 256 * 256,
+                       3 * self.n // 4 if cropped else self.n, cropped)
 
-    def prism_smatrix_view(self, buf: torch.Tensor, f: int, storage: str) -> SMatrix:
+    def prism_smatrix_view(self, buf: torch.Tensor, f: int, storage: str, cropped: bool = False) -> SMatrix:
         """An S-matrix handle on an existing buffer (e.g. one assembled from
         beam ranges built on several devices)."""
         lib = _lib.load()
-        if buf.numel() < lib.stem_prism_smatrix_bytes(self._h, f, STORAGE[storage]):
+        if buf.numel() < lib.stem_prism_smatrix_bytes(self._h, f, STORAGE[storage] | (STEM_CROPPED if cropped else 0)):
             raise ValueError("buffer smaller than the S-matrix")
         nb = len(self.prism_beams(f))
         nbp = (nb + 63) // 64 * 64
-        return SMatrix(buf, f, storage, nb, nbp, (nbp * 4 + 255) // 256 * 256, self.n)
+        return SMatrix(buf, f, storage, nb, nbp, (nbp * 4 + 255) // 256 * 256,
+                       3 * self.n // 4 if cropped else self.n, cropped)
 
     def prism_smatrix_streamed(self, trans_host: torch.Tensor, f: int, storage: str = "f32", batch: int = 128,
                                workspace: Optional[torch.Tensor] = None,
@@ -339,13 +349,15 @@ class Plan:
         if meta["tag"] != tag:
             raise ValueError(f"{path}: S-matrix belongs to specimen {meta['tag']!r}, not {tag!r}")
         lib = _lib.load()
-        nbytes = lib.stem_prism_smatrix_bytes(self._h, meta["f"], STORAGE[meta["storage"]])
+        cropped = bool(meta.get("cropped", False))
+        nbytes = lib.stem_prism_smatrix_bytes(self._h, meta["f"],
+                                              STORAGE[meta["storage"]] | (STEM_CROPPED if cropped else 0))
         nb = len(self.prism_beams(meta["f"]))
         if raw.dtype != np.uint8 or raw.size != nbytes or nb != meta["n_beams"]:
             raise ValueError(f"{path}: buffer size or beam count does not match this plan")
         buf = torch.from_numpy(raw).to(self.device)
         return SMatrix(buf, meta["f"], meta["storage"], meta["n_beams"], meta["nbp"], meta["data_offset"],
-                       meta["n"])
+                       meta["n"], cropped)
 
     def prism_output_workspace(self, f: int, chunk: int) -> torch.Tensor:
         return _workspace(_lib.load().stem_prism_output_workspace(self._h, f, chunk), self.device)
@@ -362,7 +374,7 @@ class Plan:
             rings = _need(rings, torch.float32, "rings", (npr, self.n_rings))
         chunk = int(max(1, min(chunk, max(npr, 1), 65535)))
         ws = workspace if workspace is not None else self.prism_output_workspace(smat.f, chunk)
-        check(lib.stem_prism_output(self._h, smat.f, STORAGE[smat.storage], ENGINE[engine], _ptr(smat.buf),
+        check(lib.stem_prism_output(self._h, smat.f, smat.code, ENGINE[engine], _ptr(smat.buf),
                                     _ptr(probe_xy), npr, chunk, float(weight), _ptr(rings), _ptr(ws), ws.numel(),
                                     _stream(self.device)), "stem_prism_output")
         return rings
@@ -373,12 +385,12 @@ class Plan:
         lib = _lib.load()
         probe_xy = _need(probe_xy, torch.float64, "probe_xy")
         npr = probe_xy.shape[0]
-        w = self.n // smat.f
+        w = smat.n // smat.f
         if dp is None:
             dp = torch.zeros((npr, w, w), dtype=torch.float32, device=self.device)
         chunk = int(max(1, min(chunk, max(npr, 1), 65535)))
         ws = self.prism_output_workspace(smat.f, chunk)
-        check(lib.stem_prism_output_4d(self._h, smat.f, STORAGE[smat.storage], ENGINE[engine], _ptr(smat.buf),
+        check(lib.stem_prism_output_4d(self._h, smat.f, smat.code, ENGINE[engine], _ptr(smat.buf),
                                        _ptr(probe_xy), npr, chunk, float(weight), _ptr(dp), _ptr(ws), ws.numel(),
                                        _stream(self.device)), "stem_prism_output_4d")
         return dp
@@ -387,10 +399,10 @@ class Plan:
         lib = _lib.load()
         probe_xy = _need(probe_xy, torch.float64, "probe_xy")
         npr = probe_xy.shape[0]
-        w = self.n // smat.f
+        w = smat.n // smat.f
         out = torch.empty((npr, w, w), dtype=torch.complex64, device=self.device)
         ws = self.prism_output_workspace(smat.f, max(npr, 1))
-        check(lib.stem_prism_windows(self._h, smat.f, STORAGE[smat.storage], ENGINE[engine], _ptr(smat.buf),
+        check(lib.stem_prism_windows(self._h, smat.f, smat.code, ENGINE[engine], _ptr(smat.buf),
                                      _ptr(probe_xy), npr, _ptr(out), _ptr(ws), ws.numel(), _stream(self.device)),
               "stem_prism_windows")
         return out
@@ -424,14 +436,17 @@ def fft2(x: torch.Tensor, inverse: bool = False) -> torch.Tensor:
 ALGO = {"ms": 0, "prism": 1, "ms_streamed": 2, "prism_streamed": 3}
 
 
-def footprint_bytes(w, algo: str = "ms", f: int = 1, storage: str = "f32", batch: int = 256) -> int:
+def footprint_bytes(w, algo: str = "ms", f: int = 1, storage: str = "f32", batch: int = 256,
+                    cropped: bool = False) -> int:
     """Device bytes a simulation of workload ``w`` needs (admission control).
-    algo: "ms", "prism", or their "_streamed" forms (transmission stack in host memory)."""
+    algo: "ms", "prism", or their "_streamed" forms (transmission stack in host memory);
+    cropped: a PRISM S-matrix stored Fourier-cropped."""
     lib = _lib.load()
     p = StemParams((ctypes.c_double * 3)(*[float(c) for c in w.cell]), int(w.n), int(w.n_slices),
                    float(w.slice_dz), float(w.energy_kev), float(w.alpha_mrad), float(w.ring_width_mrad),
                    int(w.n_rings), float(getattr(w, "defocus", 0.0)), float(getattr(w, "cs", 0.0)))
-    return int(lib.stem_footprint_bytes(ctypes.byref(p), ALGO[algo], f, STORAGE[storage], w.n_probes, batch))
+    return int(lib.stem_footprint_bytes(ctypes.byref(p), ALGO[algo], f,
+                                        STORAGE[storage] | (STEM_CROPPED if cropped else 0), w.n_probes, batch))
 
 
 def memory_model(w, algo: str, budget_bytes: int, f: int = 1, storage: str = "f32", batch: int = 256) -> str:

@@ -139,6 +139,19 @@ stem_status check_params(const stem_params* p) {
 // f must be a power of two with W = n / f >= 8.
 bool f_ok(const stem_plan_s* pl, int f) { return is_pow2(f) && f <= pl->n / 8; }
 
+// Storage code = element type (STEM_F32, _F16, _BF16), optionally with the
+// STEM_CROPPED flag; false for anything else.
+bool decode_storage(int storage, int* elem, bool* cropped) {
+  const int e = storage & ~(int)STEM_CROPPED;
+  if (e < STEM_F32 || e > STEM_BF16) return false;
+  *elem = e;
+  *cropped = (storage & (int)STEM_CROPPED) != 0;
+  return true;
+}
+
+// Side of the grid the S-matrix is stored on: N, or N' = 3N/4 when cropped.
+int smatrix_grid(int n, bool cropped) { return cropped ? 3 * n / 4 : n; }
+
 // Number of beams of the FP64 aperture test for a given f (used by the footprint query).
 int count_beams(const stem_params* p, int f, double lam) {
   const int n = p->n;
@@ -197,9 +210,9 @@ int build_fine_lut(const stem_params& p, double lam, const std::vector<double>& 
   return n_ap;
 }
 
-// Window table for f: window frequency (mu, nu) is the fine frequency (f mu, f nu).
-std::vector<uint16_t> coarse_lut(const std::vector<uint16_t>& lut, int n, int f) {
-  const int w = n / f;
+// Window table for f: a window spans L / f, so window frequency (mu, nu) is
+// the fine frequency (f mu, f nu); w = n / f, or 3n / (4f) on the cropped grid.
+std::vector<uint16_t> coarse_lut(const std::vector<uint16_t>& lut, int n, int f, int w) {
   std::vector<uint16_t> coarse((size_t)w * w);
   for (int v = 0; v < w; ++v) {
     const int fi = ((f * freq(v, w)) % n + n) % n;
@@ -236,6 +249,7 @@ void stem_plan_destroy(stem_plan pl) {
   cudaFree(pl->prop_y);
   for (int i = 0; i <= kMaxLog2F; ++i) {
     cudaFree(pl->lut[i]);
+    cudaFree(pl->lut_crop[i]);
     cudaFree(pl->beams[i]);
     cudaFree(pl->beam_turns[i]);
   }
@@ -285,8 +299,12 @@ stem_status stem_plan_create(const stem_params* params, stem_plan* out) {
   for (int lf = 0; lf <= kMaxLog2F; ++lf) {
     const int f = 1 << lf;
     if (f > n / 8) break;
-    const std::vector<uint16_t> coarse = coarse_lut(lut, n, f);
+    const std::vector<uint16_t> coarse = coarse_lut(lut, n, f, n / f);
     upload(reinterpret_cast<void**>(&pl->lut[lf]), coarse.data(), coarse.size() * sizeof(uint16_t));
+    if (n >= 64) {
+      const std::vector<uint16_t> crop = coarse_lut(lut, n, f, smatrix_grid(n, true) / f);
+      upload(reinterpret_cast<void**>(&pl->lut_crop[lf]), crop.data(), crop.size() * sizeof(uint16_t));
+    }
     // PRISM beams: aperture pixels on every f-th frequency, ordered by n then m.
     std::vector<int2>& bl = pl->h_beams[lf];
     for (int nn = -n / 2; nn < n / 2; ++nn) {
@@ -350,10 +368,16 @@ stem_status stem_plan_set_detector_edges(stem_plan pl, int32_t n_edges, const do
   for (int lf = 0; lf <= kMaxLog2F; ++lf) {
     const int f = 1 << lf;
     if (f > pl->n / 8 || !pl->lut[lf]) break;
-    const std::vector<uint16_t> coarse = coarse_lut(lut, pl->n, f);
+    const std::vector<uint16_t> coarse = coarse_lut(lut, pl->n, f, pl->n / f);
     if (cudaMemcpy(pl->lut[lf], coarse.data(), coarse.size() * sizeof(uint16_t), cudaMemcpyHostToDevice) !=
         cudaSuccess)
       return STEM_ERR_CUDA;
+    if (pl->lut_crop[lf]) {
+      const std::vector<uint16_t> crop = coarse_lut(lut, pl->n, f, smatrix_grid(pl->n, true) / f);
+      if (cudaMemcpy(pl->lut_crop[lf], crop.data(), crop.size() * sizeof(uint16_t), cudaMemcpyHostToDevice) !=
+          cudaSuccess)
+        return STEM_ERR_CUDA;
+    }
   }
   pl->edges = edges;
   pl->p.n_rings = p.n_rings;
@@ -477,8 +501,10 @@ stem_status stem_prism_beams(stem_plan pl, int32_t f, int32_t* n_beams, int32_t*
 }
 
 size_t stem_prism_smatrix_bytes(stem_plan pl, int32_t f, stem_storage storage) {
-  if (!pl || !f_ok(pl, f) || storage < STEM_F32 || storage > STEM_BF16) return 0;
-  return smatrix_layout(pl->n, pl->n_beams[log2i(f)], storage).total;
+  int elem;
+  bool crop;
+  if (!pl || !f_ok(pl, f) || !decode_storage(storage, &elem, &crop) || (crop && pl->n < 64)) return 0;
+  return smatrix_layout(smatrix_grid(pl->n, crop), pl->n_beams[log2i(f)], elem).total;
 }
 
 static size_t smatrix_ws_waves(int n, int batch) { return ((size_t)batch * n * n * sizeof(float2) + 255) / 256 * 256; }
@@ -498,7 +524,9 @@ size_t stem_prism_smatrix_streamed_workspace(stem_plan pl, int32_t batch) {
 static stem_status run_smatrix(stem_plan pl, const void* trans, bool streamed, int32_t f, stem_storage storage,
                                int32_t batch, void* smatrix, size_t smatrix_bytes, void* ws, size_t ws_bytes,
                                void* stream, int32_t b_begin = 0, int32_t b_end = -1) {
-  if (!pl || !trans || !smatrix || !ws || !f_ok(pl, f) || storage < STEM_F32 || storage > STEM_BF16 || batch < 1 ||
+  int elem;
+  bool crop;
+  if (!pl || !trans || !smatrix || !ws || !f_ok(pl, f) || !decode_storage(storage, &elem, &crop) || batch < 1 ||
       batch > 65535)
     return STEM_ERR_INVALID;
   const int n = pl->n;
@@ -507,7 +535,8 @@ static stem_status run_smatrix(stem_plan pl, const void* trans, bool streamed, i
   const int nb = pl->n_beams[lf];
   if (b_end < 0) b_end = nb;
   if (b_begin < 0 || b_begin > b_end || b_end > nb) return STEM_ERR_INVALID;
-  const SmatLayout L = smatrix_layout(n, nb, storage);
+  const int n_out = smatrix_grid(n, crop);
+  const SmatLayout L = smatrix_layout(n_out, nb, elem);
   const size_t need = streamed ? stem_prism_smatrix_streamed_workspace(pl, batch) : stem_prism_smatrix_workspace(pl, batch);
   if (smatrix_bytes < L.total || ws_bytes < need) return STEM_ERR_NOMEM;
   if (reinterpret_cast<uintptr_t>(smatrix) % 256) return STEM_ERR_INVALID;
@@ -532,13 +561,17 @@ static stem_status run_smatrix(stem_plan pl, const void* trans, bool streamed, i
     a.beams = pl->beams[lf] + b0;
     cudaError_t e = cudaMemsetAsync(a.beam_max, 0, a.batch * sizeof(unsigned), s);
     for (int sl = 0; sl < pl->p.n_slices && e == cudaSuccess; ++sl) {
+      const bool last = sl + 1 == pl->p.n_slices;
       e = src->acquire(sl, s, &a.trans);
       if (e == cudaSuccess) e = launch_row_pass(n, sl == 0 ? ROW_BEAM0 : ROW_SLICE, a, s);
       if (e == cudaSuccess) e = src->release(s);
-      if (e == cudaSuccess) e = launch_col_pass(n, COL_SLICE, a, s);
+      // cropped: the last column pass leaves the spectrum for the crop
+      if (e == cudaSuccess) e = launch_col_pass(n, crop && last ? COL_SPEC : COL_SLICE, a, s);
     }
-    if (e == cudaSuccess) e = launch_row_pass(n, ROW_IFFT_MAX, a, s);
-    if (e == cudaSuccess) e = launch_smatrix_store(a.wave, a.batch, n, b0, nb, a.beam_max, storage, L, smatrix, s);
+    if (e == cudaSuccess)
+      e = crop ? launch_crop_finish(a.wave, a.batch, n, a.beam_max, s) : launch_row_pass(n, ROW_IFFT_MAX, a, s);
+    if (e == cudaSuccess)
+      e = launch_smatrix_store(a.wave, a.batch, n, n_out, b0, nb, a.beam_max, elem, L, smatrix, s);
     if (e != cudaSuccess) return STEM_ERR_CUDA;
   }
   return STEM_OK;
@@ -572,17 +605,21 @@ size_t stem_prism_output_workspace(stem_plan pl, int32_t f, int32_t chunk) {
 
 static stem_status output_common(stem_plan pl, int32_t f, stem_storage storage, int32_t engine, const void* smatrix,
                                  OutputArgs& o) {
-  if (!pl || !smatrix || !f_ok(pl, f) || storage < STEM_F32 || storage > STEM_BF16) return STEM_ERR_INVALID;
+  int elem;
+  bool crop;
+  if (!pl || !smatrix || !f_ok(pl, f) || !decode_storage(storage, &elem, &crop)) return STEM_ERR_INVALID;
   if (engine < STEM_SUM_AUTO || engine > STEM_SUM_TENSOR) return STEM_ERR_INVALID;
   if (pl->n < 64) return STEM_ERR_UNSUPPORTED;
   const int lf = log2i(f);
-  const SmatLayout L = smatrix_layout(pl->n, pl->n_beams[lf], storage);
-  o.n = pl->n;
+  const int ng = smatrix_grid(pl->n, crop);
+  const SmatLayout L = smatrix_layout(ng, pl->n_beams[lf], elem);
+  o.n = ng;
   o.f = f;
-  o.w = pl->n / f;
-  o.storage = storage;
-  o.engine = engine == STEM_SUM_AUTO ? (storage == STEM_F32 ? STEM_SUM_SIMT : STEM_SUM_TENSOR) : engine;
-  if (o.engine == STEM_SUM_TENSOR && storage == STEM_F32) return STEM_ERR_UNSUPPORTED;
+  o.w = ng / f;
+  o.cropped = crop;
+  o.storage = elem;
+  o.engine = engine == STEM_SUM_AUTO ? (elem == STEM_F32 ? STEM_SUM_SIMT : STEM_SUM_TENSOR) : engine;
+  if (o.engine == STEM_SUM_TENSOR && elem == STEM_F32) return STEM_ERR_UNSUPPORTED;
   o.status = pl->status;
   o.n_beams = L.n_beams;
   o.nbp = L.nbp;
@@ -593,8 +630,8 @@ static stem_status output_common(stem_plan pl, int32_t f, stem_storage storage, 
   o.sdata = static_cast<const char*>(smatrix) + L.data_offset;
   o.lx = pl->p.cell[0];
   o.ly = pl->p.cell[1];
-  o.dx = pl->p.cell[0] / pl->n;
-  o.dy = pl->p.cell[1] / pl->n;
+  o.dx = pl->p.cell[0] / ng;
+  o.dy = pl->p.cell[1] / ng;
   o.coef_norm = (float)(1.0 / std::sqrt((double)std::max(L.n_beams, 1)));
   return STEM_OK;
 }
@@ -640,8 +677,15 @@ static stem_status run_prism_output(stem_plan pl, int32_t f, stem_storage storag
     if (rings_out) a.rings = rings_out + c0 * pl->p.n_rings;
     if (dp_out) a.dp = dp_out + c0 * (size_t)o.w * o.w;
     a.ring_scale = (float)(weight / w4);
-    if (e == cudaSuccess) e = launch_row_pass(o.w, ROW_FFT, a, s);
-    if (e == cudaSuccess) e = launch_col_pass(o.w, dp_out ? COL_DP : COL_DET, a, s);
+    if (o.cropped) {
+      // W' = 3N / (4f) windows; the band limit in coarse units is (N / f)^2
+      const int wf = pl->n / f;
+      if (e == cudaSuccess)
+        e = launch_window_fft3(o.w, windows, np, pl->lut_crop[lf], a.n_rings, a.ring_scale, a.rings, a.dp, wf * wf, s);
+    } else {
+      if (e == cudaSuccess) e = launch_row_pass(o.w, ROW_FFT, a, s);
+      if (e == cudaSuccess) e = launch_col_pass(o.w, dp_out ? COL_DP : COL_DET, a, s);
+    }
     if (e != cudaSuccess) return STEM_ERR_CUDA;
   }
   return STEM_OK;
@@ -695,8 +739,11 @@ size_t stem_footprint_bytes(const stem_params* p, int32_t algo, int32_t f, stem_
   const size_t stack = algo >= 2 ? (size_t)kStreamBufs * plane * sizeof(float2) : trans;
   if (algo == 0 || algo == 2) return stack + (size_t)batch * plane * sizeof(float2) + rings;
   if (!is_pow2(f) || f > p->n / 8) return 0;
+  int elem;
+  bool crop;
+  if (!decode_storage(storage, &elem, &crop) || (crop && p->n < 64)) return 0;
   const int nb = count_beams(p, f, wavelength_a(p->energy_kev));
-  const SmatLayout L = smatrix_layout(p->n, nb, storage);
+  const SmatLayout L = smatrix_layout(smatrix_grid(p->n, crop), nb, elem);
   const int chunk = (int)std::min<int64_t>(std::max<int64_t>(n_probes, 1), 4096);
   return stack + L.total + (size_t)batch * plane * sizeof(float2) + (size_t)batch * 4 +
          output_workspace_layout(p->n, f, chunk, L.nbp).total + rings;

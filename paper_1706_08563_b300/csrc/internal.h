@@ -40,7 +40,7 @@ struct PassArgs {
 };
 
 enum RowMode { ROW_SLICE = 0, ROW_BEAM0 = 1, ROW_IFFT_MAX = 2, ROW_FFT = 3, ROW_IFFT = 4 };
-enum ColMode { COL_SLICE = 0, COL_DET = 1, COL_PROBE_INIT = 2, COL_FFT = 3, COL_IFFT = 4, COL_DP = 5 };
+enum ColMode { COL_SLICE = 0, COL_DET = 1, COL_PROBE_INIT = 2, COL_FFT = 3, COL_IFFT = 4, COL_DP = 5, COL_SPEC = 6 };
 
 // Counts this library's kernel launches (stem_launch_count); called at every launch site.
 void note_launch();
@@ -63,9 +63,21 @@ struct SmatLayout {
 };
 SmatLayout smatrix_layout(int n, int n_beams, int storage);
 
-cudaError_t launch_smatrix_store(const float2* waves, int nb, int n, int b0, int n_beams_total,
+// waves [nb][n][n]; the stored pixels are the top-left n_out x n_out of each
+// wave (n_out = n, or N' = 3n/4 for the Fourier-cropped S-matrix)
+cudaError_t launch_smatrix_store(const float2* waves, int nb, int n, int n_out, int b0, int n_beams_total,
                                  const unsigned* beam_max, int storage, const SmatLayout& L,
                                  void* smatrix, cudaStream_t s);
+
+// Fourier-cropped S-matrix (crop.cu): from the spectra / N^2 in the in-band
+// columns of each wave [n][n] to the exit waves on the N' = 3n/4 grid in the
+// top-left N' x N' of the same buffer, with each beam's largest |Re|, |Im|.
+cudaError_t launch_crop_finish(float2* wave, int batch, int n, unsigned* beam_max, cudaStream_t s);
+// W' x W' transforms (W' = 3 * 2^k) of PRISM windows [np][W'][W'] in place, then
+// rings (lut: the window's coarse ring table) or, with dp, the 4D pattern inside
+// 9 (mu^2 + nu^2) <= band_w2.
+cudaError_t launch_window_fft3(int w, float2* win, int np, const uint16_t* lut, int n_rings, float scale,
+                               float* rings, float* dp, int band_w2, cudaStream_t s);
 
 struct OutputWs {
   size_t coef = 0, origin = 0, counts = 0, offsets = 0, work = 0, list = 0, windows = 0, total = 0;
@@ -73,7 +85,8 @@ struct OutputWs {
 OutputWs output_workspace_layout(int n, int f, int chunk, int nbp);
 
 struct OutputArgs {
-  int n = 0, f = 0, w = 0, storage = 0, engine = 0;
+  int n = 0, f = 0, w = 0, storage = 0, engine = 0;   // n, w: the S-matrix grid and window (cropped or not)
+  bool cropped = false;
   int n_beams = 0, nbp = 0;
   const int2* beams = nullptr;
   const double* beam_turns = nullptr;   // chi(k_b) / (2 pi) per beam, reduced mod 1
@@ -110,6 +123,7 @@ struct stem_plan_s {
   float2* prop_x = nullptr;
   float2* prop_y = nullptr;
   uint16_t* lut[stem::kMaxLog2F + 1] = {};
+  uint16_t* lut_crop[stem::kMaxLog2F + 1] = {};   // window tables W' x W' of the cropped S-matrix
   int2* beams[stem::kMaxLog2F + 1] = {};
   int n_beams[stem::kMaxLog2F + 1] = {};
   double* beam_turns[stem::kMaxLog2F + 1] = {};   // chi(k_b) / (2 pi) mod 1 per beam

@@ -422,10 +422,12 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, ColCfg<N>::MINB) k_col_pas
     }
 #endif
 
-    if constexpr (MODE == COL_SLICE || MODE == COL_DET || MODE == COL_FFT || MODE == COL_DP)
+    if constexpr (MODE == COL_SLICE || MODE == COL_DET || MODE == COL_FFT || MODE == COL_DP || MODE == COL_SPEC)
       fft_dist<N, false>(v, view, t, sync, tw);
 
-    if constexpr (MODE == COL_SLICE) {
+    // COL_SPEC (the last slice of a cropped S-matrix) stores the propagated
+    // spectrum M P FFT(.) / N^2 without the inverse transform
+    if constexpr (MODE == COL_SLICE || MODE == COL_SPEC) {
       const int m = signed_freq(col, N);
       const float2 px = cscale(__ldg(a.prop_x + col), a.prop_scale);
 #pragma unroll
@@ -847,6 +849,7 @@ static cudaError_t col_dispatch(int mode, const PassArgs& a, cudaStream_t s) {
     switch (mode) {
       case COL_SLICE: return col_launch<N, COL_SLICE, true>(a, s);
       case COL_PROBE_INIT: return col_launch<N, COL_PROBE_INIT, true>(a, s);
+      case COL_SPEC: return col_launch<N, COL_SPEC, true>(a, s);
       default: break;
     }
   }

@@ -63,7 +63,7 @@ __device__ __forceinline__ float pow2_scale(unsigned max_bits, int storage) {
 }
 
 template <int S>
-__global__ void k_smatrix_store(const float2* __restrict__ waves, int nb, int npix, int b0,
+__global__ void k_smatrix_store(const float2* __restrict__ waves, int nb, int n, int n_out, int b0,
                                 const unsigned* __restrict__ beam_max, int nbp, float* __restrict__ scales,
                                 typename Elem<S>::T* __restrict__ data) {
   __shared__ float2 tile[32][33];
@@ -82,7 +82,9 @@ __global__ void k_smatrix_store(const float2* __restrict__ waves, int nb, int np
   }
   for (int k = ty; k < 32; k += 8) {
     const int bl = bl0 + k;
-    tile[k][tx] = bl < nb ? waves[(size_t)bl * npix + pix0 + tx] : make_float2(0.0f, 0.0f);
+    const int pix = pix0 + tx;   // pixel (pix / n_out, pix % n_out) of the stored grid
+    tile[k][tx] = bl < nb ? waves[(size_t)bl * n * n + (size_t)(pix / n_out) * n + pix % n_out]
+                          : make_float2(0.0f, 0.0f);
   }
   __syncthreads();
   const int bl = bl0 + tx;
@@ -112,25 +114,26 @@ __global__ void k_smatrix_pad(int npix, int n_beams, int nbp, float* scales, typ
 }
 
 template <int S>
-static void store_typed(const float2* waves, int nb, int npix, int b0, int n_beams_total, const unsigned* beam_max,
-                        const SmatLayout& L, float* scales, char* data, cudaStream_t s) {
+static void store_typed(const float2* waves, int nb, int n, int n_out, int b0, int n_beams_total,
+                        const unsigned* beam_max, const SmatLayout& L, float* scales, char* data, cudaStream_t s) {
   using T = typename Elem<S>::T;
+  const int npix = n_out * n_out;
   dim3 grid(npix / 32, (nb + 31) / 32);
-  note_launch(), k_smatrix_store<S><<<grid, 256, 0, s>>>(waves, nb, npix, b0, beam_max, L.nbp, scales, reinterpret_cast<T*>(data));
+  note_launch(), k_smatrix_store<S><<<grid, 256, 0, s>>>(waves, nb, n, n_out, b0, beam_max, L.nbp, scales,
+                                                        reinterpret_cast<T*>(data));
   if (b0 + nb >= n_beams_total && L.nbp > n_beams_total)
     note_launch(), k_smatrix_pad<S><<<1024, 256, 0, s>>>(npix, n_beams_total, L.nbp, scales, reinterpret_cast<T*>(data));
 }
 
-cudaError_t launch_smatrix_store(const float2* waves, int nb, int n, int b0, int n_beams_total,
+cudaError_t launch_smatrix_store(const float2* waves, int nb, int n, int n_out, int b0, int n_beams_total,
                                  const unsigned* beam_max, int storage, const SmatLayout& L, void* smatrix,
                                  cudaStream_t s) {
   float* scales = static_cast<float*>(smatrix);
   char* data = static_cast<char*>(smatrix) + L.data_offset;
-  const int npix = n * n;
   switch (storage) {
-    case STEM_F32: store_typed<STEM_F32>(waves, nb, npix, b0, n_beams_total, beam_max, L, scales, data, s); break;
-    case STEM_F16: store_typed<STEM_F16>(waves, nb, npix, b0, n_beams_total, beam_max, L, scales, data, s); break;
-    case STEM_BF16: store_typed<STEM_BF16>(waves, nb, npix, b0, n_beams_total, beam_max, L, scales, data, s); break;
+    case STEM_F32: store_typed<STEM_F32>(waves, nb, n, n_out, b0, n_beams_total, beam_max, L, scales, data, s); break;
+    case STEM_F16: store_typed<STEM_F16>(waves, nb, n, n_out, b0, n_beams_total, beam_max, L, scales, data, s); break;
+    case STEM_BF16: store_typed<STEM_BF16>(waves, nb, n, n_out, b0, n_beams_total, beam_max, L, scales, data, s); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

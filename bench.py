@@ -704,7 +704,7 @@ def serving_mix(recipes, dev):
     return out, max_scan
 
 
-def measure_serving(dev, n_requests=24, rate_hz=4.0):
+def measure_serving(dev, n_requests=24, rate_hz=4.0, load=0.6):
     """Seeded Poisson stream of mixed multislice / PRISM requests (settings drawn
     from the serving ranges: grids 256-2048, f 1-16, 10-100 slices, scans
     16^2-256^2) through the continuous-batching server, against the same
@@ -735,15 +735,29 @@ def measure_serving(dev, n_requests=24, rate_hz=4.0):
     run_serial(reqs, device=dev)
     torch.cuda.synchronize()
     t_serial = time.perf_counter() - t0
-    # latency: Poisson arrivals, results as soon as their probes are done
+    # capacity: the requests queued at once (fresh server, no resident lanes)
+    kept = [(t, k, xy) for t, k, xy in stream if fits[k]]
+    burst = [make(k, xy) for _, k, xy in kept]
+    srv2 = Server(budget, batch=64, prism_chunk=1024, arena=65536, device=dev)
+    futs2 = [srv2.submit(r) for r in burst]
+    t0 = time.perf_counter()
+    srv2.start()
+    for fu in futs2:
+        fu.result(timeout=1800)
+    t_burst = time.perf_counter() - t0
+    srv2.stop()
+    # latency: Poisson arrivals offering about `load` of that capacity (the same
+    # seeded draws, times rescaled), results as soon as their probes are done
+    rate = load * len(reqs) / t_burst
+    kept = [(t, k, xy) for t, k, xy in W.serving_requests(recipes, n_requests, rate, scans=(16, 32, 64, 128, 256),
+                                                           max_scan=max_scan) if fits[k]]
     srv = Server(budget, batch=64, prism_chunk=1024, arena=65536, device=dev)
     srv.start()
     futs = []
     t_start = time.perf_counter()
-    kept = [(t, k, xy) for t, k, xy in stream if fits[k]]
 
     def feeder():
-        for (t_arr, k, xy), r in zip(kept, reqs):
+        for (t_arr, k, xy), r in zip(kept, [make(k, xy) for _, k, xy in kept]):
             delay = t_start + t_arr - time.perf_counter()
             if delay > 0:
                 time.sleep(delay)
@@ -755,26 +769,17 @@ def measure_serving(dev, n_requests=24, rate_hz=4.0):
         fu.result(timeout=1800)
     srv.stop()
     lat = np.array(srv.latencies) * 1e3
-    # capacity: the same requests queued at once (fresh server, no resident lanes)
-    burst = [make(k, xy) for _, k, xy in kept]
-    srv2 = Server(budget, batch=64, prism_chunk=1024, arena=65536, device=dev)
-    futs2 = [srv2.submit(r) for r in burst]
-    t0 = time.perf_counter()
-    srv2.start()
-    for fu in futs2:
-        fu.result(timeout=1800)
-    t_burst = time.perf_counter() - t0
-    srv2.stop()
     return {"requests": len(reqs), "requests_drawn": n_requests,
             "refused_by_footprint": int(sum(1 for _, k, _ in stream if not fits[k])),
-            "probes": probes, "arrival_rate_hz": rate_hz, "memory_budget_bytes": budget,
+            "probes": probes, "arrival_rate_hz": rate, "offered_load": load, "memory_budget_bytes": budget,
             "recipes": [f"{r.algo} N={r.workload.n} S={r.workload.n_slices}" + (f" f={r.f} {r.storage}" if r.algo == "prism" else "")
                         for r in recipes],
             "work_caps": {"wave_pixel_slices": SERVE_CAP_PIXEL_SLICES, "beam_sum_flop": SERVE_CAP_SUM_FLOP},
             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "burst_probes_s": probes / t_burst, "serial_probes_s": probes / t_serial,
             "speedup_vs_serial": t_serial / t_burst, "launches_poisson": srv.launches, "launches_burst": srv2.launches,
-            "what": ("p50/p99: arrival to result on the host under Poisson arrivals; burst: all requests queued at "
+            "what": ("p50/p99: arrival to result on the host under Poisson arrivals at the offered load (fraction of "
+                     "the burst capacity); burst: all requests queued at "
                      "once through the server; serial: the same requests one at a time, no overlap, no resident "
                      "potentials.  Scan sides are drawn from 16-256 and halved while a request's work is above "
                      "the caps (multislice: probes x slices x N^2; PRISM output: 8 W^2 n_beams flop per probe); "

@@ -223,11 +223,13 @@ def measure_fma_rate(lib, dev) -> dict:
 
 # --------------------------------------------------------------------------- oracle workers
 def _oracle_beam(args):
-    """Oracle exit wave of one S-matrix beam through every slice (FP64)."""
+    """Oracle exit wave of one S-matrix beam through every slice (FP64), on the
+    simulation grid or Fourier-cropped."""
     from oracle import stem as O
-    params, t_path, mn = args
+    params, t_path, mn, cropped = args
     t = np.load(t_path, mmap_mode="r")
-    return O.prism_smatrix(params, t, np.asarray([mn], dtype=np.int64))[0]
+    fn = O.prism_smatrix_cropped if cropped else O.prism_smatrix
+    return fn(params, t, np.asarray([mn], dtype=np.int64))[0]
 
 
 def _oracle_ms_rings(args):
@@ -265,7 +267,7 @@ def output_stage_error(p, sm, beams, f, xy, got, floor) -> dict:
     """The oracle's output step (window crop, beam sum, W x W FFT, rings) on the
     GPU's own S-matrix, read window by window, against the GPU's rings."""
     from oracle import stem as O
-    ref = O.prism_rings(p, sm, beams, f, xy)
+    ref = O.prism_rings(p, sm, beams, f, xy, grid=sm.n)
     return ring_errors(got, ref, floor)
 
 
@@ -510,8 +512,9 @@ def run_ours(args, rank, world, local_rank):
             picks = sorted({0, len(beams_o) // 2, len(beams_o) - 1})
             t_path = os.path.join(tmp, "trans.npy")
             np.save(t_path, trans.cpu().numpy())
-            pool = spawn_pool(min(cores, len(picks) + 4))
-            beam_futs = [pool.submit(_oracle_beam, (p, t_path, beams_o[b])) for b in picks]
+            pool = spawn_pool(min(cores, 2 * len(picks) + 4))
+            beam_futs = [pool.submit(_oracle_beam, (p, t_path, beams_o[b], False)) for b in picks]
+            crop_futs = [pool.submit(_oracle_beam, (p, t_path, beams_o[b], True)) for b in picks]
         if prism:
             res["multislice"], ms_job = measure_multislice(args, dev, hbm, src, pool, tmp)
         if prism and not args.no_error:
@@ -526,6 +529,13 @@ def run_ours(args, rank, world, local_rank):
             if not args.no_error:
                 fp32["error"] = {"bound": FP32_TOL, "output_stage": output_stage_error(
                     p, sm32, beams_o, f, xy[sample], rings32[sample], FP32_FLOOR) | {"probes": int(len(sample))}}
+        crop, smc = None, None
+        if prism and args.storage != "f32":
+            crop, smc, rings_c = measure_cropped(plan, trans, d_xyz, d_gauss, d_xy, w, f, batch, chunk, ws_pot, ws_o,
+                                                 n_probes, args.storage, sm_bytes)
+            if not args.no_error:
+                crop["error"] = {"bound": LOWP_TOL, "output_stage": output_stage_error(
+                    p, smc, beams_o, f, xy[sample], rings_c[sample], LOWP_FLOOR) | {"probes": int(len(sample))}}
         if not args.no_serving:
             res["serving"] = measure_serving(dev)
         if prism and not args.no_error:
@@ -548,9 +558,16 @@ def run_ours(args, rank, world, local_rank):
                 s32 = smatrix_stage_error(sm32, picks, oracle_beams)
                 fp32["error"]["smatrix_stage"] = {"beams": [int(b) for b in picks], "rel_l2": s32}
                 fp32["error"]["composed_first_order"] = fp32["error"]["output_stage"]["rel_l2"] + 2.0 * max(s32)
-        del sm32
+            if smc is not None:
+                c_beams = [fu.result(timeout=3600) for fu in crop_futs]
+                sc = smatrix_stage_error(smc, picks, c_beams)
+                crop["error"]["smatrix_stage"] = {"beams": [int(b) for b in picks], "rel_l2": sc}
+                crop["error"]["composed_first_order"] = crop["error"]["output_stage"]["rel_l2"] + 2.0 * max(sc)
+        del sm32, smc
         if fp32 is not None:
             res["fp32_path"] = fp32
+        if crop is not None:
+            res["cropped"] = crop
         if ms_job is not None:
             fut_list, got_ms, xy_ms, floor_ms = ms_job
             ref_ms = np.concatenate([fu.result(timeout=3600) for fu in fut_list], axis=0)
@@ -603,6 +620,50 @@ def measure_fp32_path(plan, trans, d_xyz, d_gauss, d_xy, w, f, batch, chunk, ws_
                          "smatrix": statistics.mean(e[1].elapsed_time(e[2]) for e in evs),
                          "output": statistics.mean(e[2].elapsed_time(e[3]) for e in evs)}}
     return out, holder["sm"], rings.cpu().numpy()
+
+
+def measure_cropped(plan, trans, d_xyz, d_gauss, d_xy, w, f, batch, chunk, ws_pot, ws_o, n_probes, storage,
+                    full_bytes):
+    """The same whole step with the Fourier-cropped S-matrix (3N/4 grid, W' = 3W/4
+    windows).  Returns (result, its S-matrix, rings of the last step on the host)."""
+    import torch
+    from paper_1706_08563_b300 import _lib
+    lib = _lib.load()
+    dev = trans.device
+    code = {"f16": 1, "bf16": 2}[storage] | _lib.STEM_CROPPED
+    buf = torch.empty(lib.stem_prism_smatrix_bytes(plan._h, f, code), dtype=torch.uint8, device=dev)
+    ws_s = torch.empty(lib.stem_prism_smatrix_workspace(plan._h, batch), dtype=torch.uint8, device=dev)
+    rings = torch.zeros((n_probes, w.n_rings), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    holder = {}
+
+    def one():
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        rings.zero_()
+        e[0].record(stream)
+        plan.slice_potentials(d_xyz, d_gauss, out=trans, workspace=ws_pot)
+        e[1].record(stream)
+        holder["sm"] = plan.prism_smatrix(trans, f, storage, batch=batch, workspace=ws_s, out=buf, cropped=True)
+        e[2].record(stream)
+        plan.prism_output(holder["sm"], d_xy, chunk=chunk, rings=rings, workspace=ws_o)
+        e[3].record(stream)
+        return e
+    one()
+    torch.cuda.synchronize()
+    evs = [one() for _ in range(2)]
+    torch.cuda.synchronize()
+    tot = [e[0].elapsed_time(e[3]) for e in evs]
+    sm = holder["sm"]
+    out = {"value": n_probes / (statistics.mean(tot) / 1e3), "unit": "probes/s", "ms_per_step": statistics.mean(tot),
+           "steps": 2, "warmup": 1, "smatrix_storage": storage + " Fourier-cropped",
+           "grid": sm.n, "window": sm.n // f, "smatrix_bytes": int(buf.numel()),
+           "smatrix_bytes_uncropped": int(full_bytes),
+           "phases_ms": {"potentials": statistics.mean(e[0].elapsed_time(e[1]) for e in evs),
+                         "smatrix": statistics.mean(e[1].elapsed_time(e[2]) for e in evs),
+                         "output": statistics.mean(e[2].elapsed_time(e[3]) for e in evs)},
+           "what": "S-matrix stored on the 3N/4 grid that holds the 2/3 band exactly; windows of 3W/4 pixels over "
+                   "the same L/f; a different (Fourier-interpolated) sampling, checked against its own oracle"}
+    return out, sm, rings.cpu().numpy()
 
 
 def measure_multislice(args, dev, hbm, src, pool, tmp):

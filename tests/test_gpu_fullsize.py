@@ -97,3 +97,28 @@ def test_prism8_output_sampled_probes(prism8):
     for k, i in enumerate(pick):
         assert _rel(rings[i], ref[k]) <= 1e-2, i
     check_rings(rings[pick], ref, 1e-2)
+
+
+def test_prism8_cropped_sampled(prism8):
+    """The Fourier-cropped S-matrix at the bench size (2048^2 -> 1536^2, FP16,
+    tensor-core beam sum, windows of 192): one sampled beam through all 100
+    slices against the oracle's cropped exit wave, and the rings of sampled
+    probes of a 4096-probe chunk against the oracle's output step on the GPU's
+    own cropped S-matrix, read window by window."""
+    w, xyz, gauss, plan, trans, v, sm = prism8
+    p = O.params_from(w)
+    beams = O.prism_beams(p, 8)
+    smc = plan.prism_smatrix(trans, 8, "f16", batch=w.batch, cropped=True)
+    assert smc.n == 1536 and smc.n_beams == 793
+    assert smc.buf.numel() < 0.57 * sm.buf.numel()
+    t = trans.cpu().numpy().astype(np.complex128)
+    ref = O.prism_smatrix_cropped(p, t, beams[396:397])[0]
+    d = smc.data()[:, :, :, 396].double().cpu().numpy()
+    got = (d[:, :, 0] + 1j * d[:, :, 1]) * float(smc.scales()[396])
+    assert _rel(got, ref) <= 2e-3
+    xy_all = W.scan_positions(w)[:4096]
+    rings = plan.prism_output(smc, torch.from_numpy(xy_all).cuda(), chunk=4096).cpu().numpy()
+    pick = np.array(list(range(0, 4096, 256)) + [4095])
+    refr = O.prism_rings(p, smc, beams, 8, xy_all[pick], grid=1536)
+    check_rings(rings[pick], refr, 1e-2)
+    assert plan.device_status() == 0

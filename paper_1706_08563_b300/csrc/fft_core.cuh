@@ -286,13 +286,50 @@ __device__ __forceinline__ void fft_dist(float2 (&v)[FftShape<N>::E], const View
   }
 }
 
+// Twiddles of one stage held in registers: when a thread's butterflies j = t + i T
+// have tile-independent q = j mod NS (always, since t is fixed per thread), a
+// kernel can load them once (load_stage_twiddles) and save the shared-memory
+// reads of every later transform.  wr[i][r - 1] = w^(r q_i).
+template <int N, int E, int R, int NS>
+__device__ __forceinline__ void load_stage_twiddles(float2 (&wr)[E / R][R - 1], int t, const float2* tw) {
+  constexpr int T = N / E;
+#pragma unroll
+  for (int i = 0; i < E / R; ++i) {
+    const int q = (t + i * T) & (NS - 1);
+#pragma unroll
+    for (int r = 1; r < R; ++r) wr[i][r - 1] = tw[(r - 1) * NS + q];
+  }
+}
+
+template <int N, int E, int R, bool INV>
+__device__ __forceinline__ void stage_compute_reg(float2 (&v)[E], const float2 (&wr)[E / R][R - 1]) {
+#pragma unroll
+  for (int i = 0; i < E / R; ++i) {
+#pragma unroll
+    for (int r = 1; r < R; ++r) {
+      const float2 w = wr[i][r - 1];
+      v[i * R + r] = INV ? cmulc(v[i * R + r], w) : cmul(v[i * R + r], w);
+    }
+    dft<R, INV>(&v[i * R]);
+  }
+}
+
+// Registers that hold the twiddles of stage 1 (W1) and stage 2 (W2) of a
+// three-stage transform, for fft_dist_x2 with TW1 / TW2 set.
+template <int N> struct StageTwiddles {
+  using S = FftShape<N>;
+  float2 w1[S::R1 > 1 ? S::E / S::R1 : 1][S::R1 > 1 ? S::R1 - 1 : 1];
+  float2 w2[S::R2 > 1 ? S::E / S::R2 : 1][S::R2 > 1 ? S::R2 - 1 : 1];
+};
+
 // Two independent transforms of the same length (rows a and b) stage by stage,
 // sharing the barriers: the instructions of one fill the latencies of the
 // other, and a row costs half the barriers.  sa and sb are separate exchange
 // buffers.  Same register conventions as fft_dist.
-template <int N, bool INV, class View, class Sync>
+template <int N, bool INV, bool TW1 = false, bool TW2 = false, class View, class Sync>
 __device__ __forceinline__ void fft_dist_x2(float2 (&va)[FftShape<N>::E], float2 (&vb)[FftShape<N>::E],
-                                            const View& sa, const View& sb, int t, Sync sync, const float2* tw) {
+                                            const View& sa, const View& sb, int t, Sync sync, const float2* tw,
+                                            const StageTwiddles<N>* reg = nullptr) {
   using S = FftShape<N>;
   using L = TwLayout<N>;
   constexpr int E = S::E;
@@ -308,8 +345,13 @@ __device__ __forceinline__ void fft_dist_x2(float2 (&va)[FftShape<N>::E], float2
     sync();
     stage_load<N, E, S::R1>(va, sa, t);
     stage_load<N, E, S::R1>(vb, sb, t);
-    stage_compute<N, E, S::R1, E, INV>(va, t, tw);
-    stage_compute<N, E, S::R1, E, INV>(vb, t, tw);
+    if constexpr (TW1) {
+      stage_compute_reg<N, E, S::R1, INV>(va, reg->w1);
+      stage_compute_reg<N, E, S::R1, INV>(vb, reg->w1);
+    } else {
+      stage_compute<N, E, S::R1, E, INV>(va, t, tw);
+      stage_compute<N, E, S::R1, E, INV>(vb, t, tw);
+    }
     if constexpr (S::R2 > 1) {
       sync();
       stage_store<N, E, S::R1, E>(va, sa, t);
@@ -317,8 +359,13 @@ __device__ __forceinline__ void fft_dist_x2(float2 (&va)[FftShape<N>::E], float2
       sync();
       stage_load<N, E, S::R2>(va, sa, t);
       stage_load<N, E, S::R2>(vb, sb, t);
-      stage_compute<N, E, S::R2, E * S::R1, INV>(va, t, tw + L::OFF2);
-      stage_compute<N, E, S::R2, E * S::R1, INV>(vb, t, tw + L::OFF2);
+      if constexpr (TW2) {
+        stage_compute_reg<N, E, S::R2, INV>(va, reg->w2);
+        stage_compute_reg<N, E, S::R2, INV>(vb, reg->w2);
+      } else {
+        stage_compute<N, E, S::R2, E * S::R1, INV>(va, t, tw + L::OFF2);
+        stage_compute<N, E, S::R2, E * S::R1, INV>(vb, t, tw + L::OFF2);
+      }
       stage_rename<E, S::R2>(va);
       stage_rename<E, S::R2>(vb);
     } else {

@@ -245,8 +245,20 @@ __global__ void __launch_bounds__(RowCfg<N>::THREADS, RowCfg<N>::MINB) k_row_pas
 #ifndef STEM_ROW_PAIR
 #define STEM_ROW_PAIR 1
 #endif
+// Stage-1 / stage-2 twiddles of the pair's transforms held in registers.  A
+// thread's butterflies have the same twiddles in every tile, so the stage-2
+// ones (14 complex values) are loaded once per CTA: 164 registers, still three
+// CTAs per SM (the register bound of __launch_bounds__(128, 3) would force 168
+// and spill), 1.3% off the slice loop at 2048; the stage-1 ones as well would
+// leave two CTAs per SM (no gain).
+#ifndef STEM_ROW_PAIR_TW1
+#define STEM_ROW_PAIR_TW1 0
+#endif
+#ifndef STEM_ROW_PAIR_TW2
+#define STEM_ROW_PAIR_TW2 1
+#endif
 #ifndef STEM_ROW_PAIR_MINB
-#define STEM_ROW_PAIR_MINB 3
+#define STEM_ROW_PAIR_MINB (STEM_ROW_PAIR_TW2 ? 2 : 3)
 #endif
 struct RowPairCfg {
   static constexpr int N = 2048, E = FftShape<N>::E, T = N / E, THREADS = T;
@@ -273,6 +285,10 @@ __global__ void __launch_bounds__(RowPairCfg::THREADS, STEM_ROW_PAIR_MINB)
   const int t = threadIdx.x;
   const SmemView<E, 1> va{xa}, vb{xb};
   auto sync = [] { __syncthreads(); };
+  constexpr bool TW1 = STEM_ROW_PAIR_TW1, TW2 = STEM_ROW_PAIR_TW2;
+  StageTwiddles<N> reg;
+  if constexpr (TW1) load_stage_twiddles<N, E, FftShape<N>::R1, E>(reg.w1, t, tw);
+  if constexpr (TW2) load_stage_twiddles<N, E, FftShape<N>::R2, E * FftShape<N>::R1>(reg.w2, t, tw + TwLayout<N>::OFF2);
   const int pairs = (a.batch + 1) / 2;
   const int per = (n_tiles + gridDim.x - 1) / gridDim.x;
   const int tile_end = min(n_tiles, (int)(blockIdx.x + 1) * per);
@@ -316,7 +332,7 @@ __global__ void __launch_bounds__(RowPairCfg::THREADS, STEM_ROW_PAIR_MINB)
       }
     }
 #endif
-    fft_dist_x2<N, true>(A, B, va, vb, t, sync, tw);
+    fft_dist_x2<N, true, TW1, TW2>(A, B, va, vb, t, sync, tw, &reg);
     if (fresh) {
       const bool ok = mbar_wait(smem_u32(tbar), tphase);
       tphase ^= 1u;
@@ -335,7 +351,7 @@ __global__ void __launch_bounds__(RowPairCfg::THREADS, STEM_ROW_PAIR_MINB)
       A[q] = cmul(A[q], tv);
       B[q] = cmul(B[q], tv);
     }
-    fft_dist_x2<N, false>(A, B, va, vb, t, sync, tw);
+    fft_dist_x2<N, false, TW1, TW2>(A, B, va, vb, t, sync, tw, &reg);
 #pragma unroll
     for (int q = 0; q < E; ++q) {
       const int x = t + q * T;

@@ -71,6 +71,7 @@ def parse():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-error", action="store_true", help="skip the stated-error measurement against the oracle")
     ap.add_argument("--no-fp32-path", action="store_true", help="skip the FP32-storage / CUDA-core comparison leg")
+    ap.add_argument("--no-cropped", action="store_true", help="skip the Fourier-cropped S-matrix leg")
     ap.add_argument("--prism-split", action="store_true",
                     help="one PRISM simulation split over the ranks (beams for the S-matrix, one all-reduce, then "
                          "probes; strong scaling) instead of one whole simulation per rank")
@@ -530,7 +531,7 @@ def run_ours(args, rank, world, local_rank):
                 fp32["error"] = {"bound": FP32_TOL, "output_stage": output_stage_error(
                     p, sm32, beams_o, f, xy[sample], rings32[sample], FP32_FLOOR) | {"probes": int(len(sample))}}
         crop, smc = None, None
-        if prism and args.storage != "f32":
+        if prism and args.storage != "f32" and not args.no_cropped:
             crop, smc, rings_c = measure_cropped(plan, trans, d_xyz, d_gauss, d_xy, w, f, batch, chunk, ws_pot, ws_o,
                                                  n_probes, args.storage, sm_bytes)
             if not args.no_error:

@@ -13,6 +13,7 @@ Cases
   ms1024    multislice at the 1024^2 bench geometry: 4 slices, 32 probes
   smat2048  S-matrix, 2048^2, f=8, FP16 storage, 2 slices (793 beams, batches of 128)
   out2048   PRISM f=8 output for 4096 probes from a 2-slice S-matrix (FP16)
+  smat2048c, out2048c  the same with the Fourier-cropped S-matrix (1536^2, windows of 192)
 """
 from __future__ import annotations
 
@@ -30,7 +31,7 @@ import torch  # noqa: E402
 import workloads as W  # noqa: E402
 from paper_1706_08563_b300 import api  # noqa: E402
 
-CASES = ("ms2048", "ms1024", "smat2048", "out2048")
+CASES = ("ms2048", "ms1024", "smat2048", "out2048", "smat2048c", "out2048c")
 
 
 def _timed(fn, repeat):
@@ -48,7 +49,7 @@ def _timed(fn, repeat):
 
 def run(case: str, repeat: int = 1) -> dict:
     dev = torch.device("cuda", torch.cuda.current_device())
-    if case in ("ms2048", "smat2048", "out2048"):
+    if case in ("ms2048", "smat2048", "out2048", "smat2048c", "out2048c"):
         base = W.C4
         slices = 4 if case == "ms2048" else 2
     else:
@@ -74,10 +75,12 @@ def run(case: str, repeat: int = 1) -> dict:
                          device=dev)
         holder = {}
 
+        cropped = case.endswith("c")
+
         def smat():
-            holder["sm"] = plan.prism_smatrix(trans, f, "f16", batch=128, workspace=ws)
-        t_s = _timed(smat, repeat if case == "smat2048" else 1)
-        if case == "smat2048":
+            holder["sm"] = plan.prism_smatrix(trans, f, "f16", batch=128, workspace=ws, cropped=cropped)
+        t_s = _timed(smat, repeat if case.startswith("smat") else 1)
+        if case.startswith("smat"):
             res["ms_per_call"] = t_s
             res["beams"] = holder["sm"].n_beams
         else:

@@ -24,12 +24,12 @@ namespace stem {
 
 constexpr int gcd_c(int a, int b) { return b == 0 ? a : gcd_c(b, a % b); }
 
-// Lines (rows or columns) per CTA: as many as fit in 256 threads with the
+// Lines (rows or columns) per CTA: as many as fit in 384 threads with the
 // CTA a whole number of warps (the ring sums use warp primitives).
 template <int M> struct LineCta {
   using C = Fft3Cfg<M>;
   static constexpr int STEP = 32 / gcd_c(C::THREADS, 32);   // lines per whole number of warps
-  static constexpr int G0 = (256 / C::THREADS) / STEP * STEP;
+  static constexpr int G0 = (384 / C::THREADS) / STEP * STEP;
   static constexpr int G = G0 > 0 ? G0 : STEP;
   static constexpr int THREADS = G * C::THREADS;
   static constexpr size_t SMEM = ((size_t)G * C::LINE + C::TW) * sizeof(float2);
@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(LineCta<M>::THREADS) k_crop_cols(float2* __res
     smem[gl * C::LINE + j] = val;
   }
   __syncthreads();
-  fft3m_line<M, true>(smem + g * C::LINE, smem + g * C::LINE + L, tw, lt, [] { __syncthreads(); });
+  fft3m_line<M, true>(smem + g * C::LINE, smem + g * C::LINE, tw, lt, [] { __syncthreads(); });
   for (int i = threadIdx.x; i < G * L; i += K::THREADS) {
     const int gl = i % G, j = i / G, line = base + gl;
     if (line < n_lines) {
@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(LineCta<M>::THREADS) k_crop_rows(float2* __res
     smem[gl * C::LINE + j] = val;
   }
   __syncthreads();
-  fft3m_line<M, true>(smem + g * C::LINE, smem + g * C::LINE + L, tw, lt, [] { __syncthreads(); });
+  fft3m_line<M, true>(smem + g * C::LINE, smem + g * C::LINE, tw, lt, [] { __syncthreads(); });
   for (int i = threadIdx.x; i < G * L; i += K::THREADS) {
     const int gl = i / L, j = i % L, line = base + gl;
     if (line < n_lines) {
@@ -149,7 +149,7 @@ __global__ void __launch_bounds__(LineCta<M>::THREADS) k_win_rows(float2* __rest
     smem[gl * C::LINE + j] = base + gl < (size_t)n_lines ? win[(base + gl) * L + j] : make_float2(0.0f, 0.0f);
   }
   __syncthreads();
-  fft3m_line<M, false>(smem + g * C::LINE, smem + g * C::LINE + L, tw, lt, [] { __syncthreads(); });
+  fft3m_line<M, false>(smem + g * C::LINE, smem + g * C::LINE, tw, lt, [] { __syncthreads(); });
   for (int i = threadIdx.x; i < G * L; i += K::THREADS) {
     const int gl = i / L, j = i % L;
     if (base + gl < (size_t)n_lines) win[(base + gl) * L + j] = smem[gl * C::LINE + j];
@@ -182,7 +182,7 @@ __global__ void __launch_bounds__(LineCta<M>::THREADS)
       smem[gl * C::LINE + j] = u < L ? src[(size_t)j * L + u] : make_float2(0.0f, 0.0f);
     }
     __syncthreads();
-    fft3m_line<M, false>(smem + g * C::LINE, smem + g * C::LINE + L, tw, lt, [] { __syncthreads(); });
+    fft3m_line<M, false>(smem + g * C::LINE, smem + g * C::LINE, tw, lt, [] { __syncthreads(); });
     // consecutive threads walk down a column, along which the ring changes rarely
     constexpr int ITER = (G * L + K::THREADS - 1) / K::THREADS;
     for (int it = 0; it < ITER; ++it) {

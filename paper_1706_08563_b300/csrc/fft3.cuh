@@ -24,7 +24,10 @@ template <int M> struct Fft3Cfg {
   static constexpr int TM = DIRECT ? 1 : M / E;
   static constexpr int THREADS = DIRECT ? 32 : 3 * TM;       // threads per line
   static constexpr int XCH = DIRECT ? 0 : M + M / E;          // exchange buffer of one sub-transform
-  static constexpr int LINE = L + 3 * XCH;                    // float2 of shared memory per line
+  // float2 of shared memory per line: the line and the three exchange buffers
+  // share it (the line is read into registers before the sub-transforms'
+  // first exchange and written back after their last one)
+  static constexpr int LINE = L > 3 * XCH ? L : 3 * XCH;
   static constexpr int TW = DIRECT ? 0 : TwLayout<(M < 8 ? 8 : M)>::TOTAL;
 };
 
@@ -32,8 +35,9 @@ template <int M> struct Fft3Cfg {
 constexpr float kHalfSqrt3 = 0.8660254037844386f;
 
 // One length-3M transform of the line x (shared memory, natural order), in
-// place; exch: 3 * XCH float2 of this line; tw: the CTA's table
-// (build_twiddles<M>); tid: thread index within the line's THREADS.
+// place; exch: 3 * XCH float2 for the sub-transforms' exchanges, which may be
+// x itself; tw: the CTA's table (build_twiddles<M>); tid: thread index within
+// the line's THREADS.
 template <int M, bool INV, class Sync>
 __device__ __forceinline__ void fft3m_line(float2* x, float2* exch, const float2* tw, int tid, Sync sync) {
   using C = Fft3Cfg<M>;
@@ -66,6 +70,7 @@ __device__ __forceinline__ void fft3m_line(float2* x, float2* exch, const float2
     float2 v[E];
 #pragma unroll
     for (int q = 0; q < E; ++q) v[q] = x[3 * (t + TM * q) + r];
+    sync();   // the line is in registers before any exchange overwrites it
     const SmemView<E, 1> view{exch + r * C::XCH};
     fft_dist<M, INV>(v, view, t, sync, tw);
     sync();   // every thread has read its inputs from x (fft_dist<8> has no barrier of its own)

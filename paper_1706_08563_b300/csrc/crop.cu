@@ -24,12 +24,13 @@ namespace stem {
 
 constexpr int gcd_c(int a, int b) { return b == 0 ? a : gcd_c(b, a % b); }
 
-// Lines (rows or columns) per CTA: as many as fit in 384 threads with the
-// CTA a whole number of warps (the ring sums use warp primitives).
+// Lines (rows or columns) per CTA: as many as fit in 384 threads (192 for the
+// long transforms, whose ~100 registers would otherwise leave one CTA per SM)
+// with the CTA a whole number of warps (the ring sums use warp primitives).
 template <int M> struct LineCta {
   using C = Fft3Cfg<M>;
   static constexpr int STEP = 32 / gcd_c(C::THREADS, 32);   // lines per whole number of warps
-  static constexpr int G0 = (384 / C::THREADS) / STEP * STEP;
+  static constexpr int G0 = ((M >= 256 ? 192 : 384) / C::THREADS) / STEP * STEP;
   static constexpr int G = G0 > 0 ? G0 : STEP;
   static constexpr int THREADS = G * C::THREADS;
   static constexpr size_t SMEM = ((size_t)G * C::LINE + C::TW) * sizeof(float2);
@@ -61,33 +62,24 @@ __global__ void __launch_bounds__(LineCta<M>::THREADS) k_crop_cols(float2* __res
   const int g = threadIdx.x / C::THREADS, lt = threadIdx.x % C::THREADS;
   const int base = blockIdx.x * G;
   const int nb3 = n / 3;
-  auto column = [&](int line, int& w) {
-    w = line / nband;
-    const int cb = line % nband;
-    return cb <= nb3 ? cb : n - (nband - cb);
-  };
-  // consecutive threads take consecutive lines (neighbouring columns) of a row
+  // consecutive threads take consecutive lines (neighbouring columns) of a row;
+  // K::THREADS is a multiple of G, so a thread always serves the same line
+  const int gl = threadIdx.x % G, line = base + gl;
+  const bool valid = line < n_lines;
+  const int w = line / nband, cb = line % nband;
+  const int col = cb <= nb3 ? cb : n - (nband - cb);
+  float2* colp = wave + (size_t)w * n * n + col;
   for (int i = threadIdx.x; i < G * L; i += K::THREADS) {
-    const int gl = i % G, j = i / G, line = base + gl;
-    float2 val = make_float2(0.0f, 0.0f);
-    if (line < n_lines) {
-      int w;
-      const int col = column(line, w);
-      const int row = (sfreq(j, L) + n) % n;
-      val = wave[((size_t)w * n + row) * n + col];
-    }
-    smem[gl * C::LINE + j] = val;
+    const int j = i / G;
+    smem[gl * C::LINE + j] = valid ? colp[(size_t)((sfreq(j, L) + n) & (n - 1)) * n] : make_float2(0.0f, 0.0f);
   }
   __syncthreads();
   fft3m_line<M, true>(smem + g * C::LINE, smem + g * C::LINE, tw, lt, [] { __syncthreads(); });
-  for (int i = threadIdx.x; i < G * L; i += K::THREADS) {
-    const int gl = i % G, j = i / G, line = base + gl;
-    if (line < n_lines) {
-      int w;
-      const int col = column(line, w);
-      wave[((size_t)w * n + j) * n + col] = smem[gl * C::LINE + j];
+  if (valid)
+    for (int i = threadIdx.x; i < G * L; i += K::THREADS) {
+      const int j = i / G;
+      colp[(size_t)j * n] = smem[gl * C::LINE + j];
     }
-  }
 }
 
 template <int M>
@@ -111,7 +103,7 @@ __global__ void __launch_bounds__(LineCta<M>::THREADS) k_crop_rows(float2* __res
     const int m = sfreq(j, L);
     if (line < n_lines && m <= nb3 && m >= -nb3) {
       const int w = line / L, y = line % L;
-      val = wave[((size_t)w * n + y) * n + (m + n) % n];
+      val = wave[((size_t)w * n + y) * n + ((m + n) & (n - 1))];
     }
     smem[gl * C::LINE + j] = val;
   }
@@ -119,11 +111,20 @@ __global__ void __launch_bounds__(LineCta<M>::THREADS) k_crop_rows(float2* __res
   fft3m_line<M, true>(smem + g * C::LINE, smem + g * C::LINE, tw, lt, [] { __syncthreads(); });
   for (int i = threadIdx.x; i < G * L; i += K::THREADS) {
     const int gl = i / L, j = i % L, line = base + gl;
+    float mx = 0.0f;
     if (line < n_lines) {
       const int w = line / L, y = line % L;
       const float2 v = smem[gl * C::LINE + j];
       wave[((size_t)w * n + y) * n + j] = v;
-      atomicMax(s_max + gl, __float_as_uint(fmaxf(fabsf(v.x), fabsf(v.y))));
+      mx = fmaxf(fabsf(v.x), fabsf(v.y));
+    }
+    if constexpr (L % 32 == 0) {
+      // the lanes of a warp share a row: one atomic per warp
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      if ((threadIdx.x & 31) == 0 && line < n_lines) atomicMax(s_max + gl, __float_as_uint(mx));
+    } else {
+      if (line < n_lines) atomicMax(s_max + gl, __float_as_uint(mx));
     }
   }
   __syncthreads();

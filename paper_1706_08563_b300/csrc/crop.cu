@@ -69,6 +69,8 @@ __global__ void __launch_bounds__(LineCta<M>::THREADS) k_crop_cols(float2* __res
   const int w = line / nband, cb = line % nband;
   const int col = cb <= nb3 ? cb : n - (nband - cb);
   float2* colp = wave + (size_t)w * n * n + col;
+  // loads batched ahead of their shared-memory stores (no wait per element)
+#pragma unroll 8
   for (int i = threadIdx.x; i < G * L; i += K::THREADS) {
     const int j = i / G;
     smem[gl * C::LINE + j] = valid ? colp[(size_t)((sfreq(j, L) + n) & (n - 1)) * n] : make_float2(0.0f, 0.0f);
@@ -97,6 +99,8 @@ __global__ void __launch_bounds__(LineCta<M>::THREADS) k_crop_rows(float2* __res
   const int base = blockIdx.x * G;
   const int nb3 = n / 3;
   // consecutive threads take consecutive entries of a row
+  // loads batched ahead of their shared-memory stores (no wait per element)
+#pragma unroll 8
   for (int i = threadIdx.x; i < G * L; i += K::THREADS) {
     const int gl = i / L, j = i % L, line = base + gl;
     float2 val = make_float2(0.0f, 0.0f);
@@ -145,6 +149,8 @@ __global__ void __launch_bounds__(LineCta<M>::THREADS) k_win_rows(float2* __rest
   line_setup<M>(smem, tw);
   const int g = threadIdx.x / C::THREADS, lt = threadIdx.x % C::THREADS;
   const size_t base = (size_t)blockIdx.x * G;
+  // loads batched ahead of their shared-memory stores (no wait per element)
+#pragma unroll 8
   for (int i = threadIdx.x; i < G * L; i += K::THREADS) {
     const int gl = i / L, j = i % L;
     smem[gl * C::LINE + j] = base + gl < (size_t)n_lines ? win[(base + gl) * L + j] : make_float2(0.0f, 0.0f);
@@ -178,6 +184,8 @@ __global__ void __launch_bounds__(LineCta<M>::THREADS)
   if constexpr (!DP)
     for (int i = threadIdx.x; i < n_rings; i += K::THREADS) ring_acc[i] = 0.0f;
   for (int u0 = 0; u0 < L; u0 += G) {
+    // loads batched ahead of their shared-memory stores (no wait per element)
+#pragma unroll 8
     for (int i = threadIdx.x; i < G * L; i += K::THREADS) {
       const int gl = i % G, j = i / G, u = u0 + gl;
       smem[gl * C::LINE + j] = u < L ? src[(size_t)j * L + u] : make_float2(0.0f, 0.0f);

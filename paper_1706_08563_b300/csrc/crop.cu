@@ -98,37 +98,39 @@ __global__ void __launch_bounds__(LineCta<M>::THREADS) k_crop_rows(float2* __res
   const int g = threadIdx.x / C::THREADS, lt = threadIdx.x % C::THREADS;
   const int base = blockIdx.x * G;
   const int nb3 = n / 3;
-  // consecutive threads take consecutive entries of a row
-  // loads batched ahead of their shared-memory stores (no wait per element)
+  // the CTA walks its lines one after the other, consecutive threads on
+  // consecutive entries of the row (line-wide indices computed once per line)
+  for (int gl = 0; gl < G; ++gl) {
+    const int line = base + gl;
+    const bool valid = line < n_lines;
+    const float2* src = wave + ((size_t)(line / L) * n + line % L) * n;
 #pragma unroll 8
-  for (int i = threadIdx.x; i < G * L; i += K::THREADS) {
-    const int gl = i / L, j = i % L, line = base + gl;
-    float2 val = make_float2(0.0f, 0.0f);
-    const int m = sfreq(j, L);
-    if (line < n_lines && m <= nb3 && m >= -nb3) {
-      const int w = line / L, y = line % L;
-      val = wave[((size_t)w * n + y) * n + ((m + n) & (n - 1))];
+    for (int j0 = 0; j0 < L; j0 += K::THREADS) {
+      const int j = j0 + threadIdx.x;
+      if (j < L) {
+        const int m = sfreq(j, L);
+        smem[gl * C::LINE + j] = valid && m <= nb3 && m >= -nb3 ? src[(m + n) & (n - 1)] : make_float2(0.0f, 0.0f);
+      }
     }
-    smem[gl * C::LINE + j] = val;
   }
   __syncthreads();
   fft3m_line<M, true>(smem + g * C::LINE, smem + g * C::LINE, tw, lt, [] { __syncthreads(); });
-  for (int i = threadIdx.x; i < G * L; i += K::THREADS) {
-    const int gl = i / L, j = i % L, line = base + gl;
-    float mx = 0.0f;
-    if (line < n_lines) {
-      const int w = line / L, y = line % L;
-      const float2 v = smem[gl * C::LINE + j];
-      wave[((size_t)w * n + y) * n + j] = v;
-      mx = fmaxf(fabsf(v.x), fabsf(v.y));
-    }
-    if constexpr (L % 32 == 0) {
-      // the lanes of a warp share a row: one atomic per warp
+  for (int gl = 0; gl < G; ++gl) {
+    const int line = base + gl;
+    const bool valid = line < n_lines;
+    float2* dst = wave + ((size_t)(line / L) * n + line % L) * n;
+    for (int j0 = 0; j0 < L; j0 += K::THREADS) {
+      const int j = j0 + threadIdx.x;
+      float mx = 0.0f;
+      if (valid && j < L) {
+        const float2 v = smem[gl * C::LINE + j];
+        dst[j] = v;
+        mx = fmaxf(fabsf(v.x), fabsf(v.y));
+      }
+      // every lane takes part (uniform trip count); one atomic per warp
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-      if ((threadIdx.x & 31) == 0 && line < n_lines) atomicMax(s_max + gl, __float_as_uint(mx));
-    } else {
-      if (line < n_lines) atomicMax(s_max + gl, __float_as_uint(mx));
+      if ((threadIdx.x & 31) == 0 && valid) atomicMax(s_max + gl, __float_as_uint(mx));
     }
   }
   __syncthreads();

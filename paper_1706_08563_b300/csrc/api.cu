@@ -210,6 +210,14 @@ int build_fine_lut(const stem_params& p, double lam, const std::vector<double>& 
   return n_ap;
 }
 
+// The fine table transposed, [x][y]: column-wise reads become contiguous.
+std::vector<uint16_t> transpose_lut(const std::vector<uint16_t>& lut, int n) {
+  std::vector<uint16_t> t((size_t)n * n);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) t[(size_t)j * n + i] = lut[(size_t)i * n + j];
+  return t;
+}
+
 // Window table for f: a window spans L / f, so window frequency (mu, nu) is
 // the fine frequency (f mu, f nu); w = n / f, or 3n / (4f) on the cropped grid.
 std::vector<uint16_t> coarse_lut(const std::vector<uint16_t>& lut, int n, int f, int w) {
@@ -250,6 +258,7 @@ void stem_plan_destroy(stem_plan pl) {
   for (int i = 0; i <= kMaxLog2F; ++i) {
     cudaFree(pl->lut[i]);
     cudaFree(pl->lut_crop[i]);
+    if (i == 0) cudaFree(pl->lut_t);
     cudaFree(pl->beams[i]);
     cudaFree(pl->beam_turns[i]);
   }
@@ -296,6 +305,10 @@ stem_status stem_plan_create(const stem_params* params, stem_plan* out) {
   upload(reinterpret_cast<void**>(&pl->prop_x), px.data(), n * sizeof(float2));
   upload(reinterpret_cast<void**>(&pl->prop_y), py.data(), n * sizeof(float2));
 
+  {
+    const std::vector<uint16_t> lt = transpose_lut(lut, n);
+    upload(reinterpret_cast<void**>(&pl->lut_t), lt.data(), lt.size() * sizeof(uint16_t));
+  }
   for (int lf = 0; lf <= kMaxLog2F; ++lf) {
     const int f = 1 << lf;
     if (f > n / 8) break;
@@ -365,6 +378,11 @@ stem_status stem_plan_set_detector_edges(stem_plan pl, int32_t n_edges, const do
   p.n_rings = n_edges - 1;
   std::vector<uint16_t> lut;
   build_fine_lut(p, pl->lam, edges, lut);
+  {
+    const std::vector<uint16_t> lt = transpose_lut(lut, pl->n);
+    if (cudaMemcpy(pl->lut_t, lt.data(), lt.size() * sizeof(uint16_t), cudaMemcpyHostToDevice) != cudaSuccess)
+      return STEM_ERR_CUDA;
+  }
   for (int lf = 0; lf <= kMaxLog2F; ++lf) {
     const int f = 1 << lf;
     if (f > pl->n / 8 || !pl->lut[lf]) break;
@@ -433,6 +451,7 @@ static stem_status run_multislice(stem_plan pl, const void* trans, bool streamed
   a.prop_y = pl->prop_y;
   a.prop_scale = 1.0f / (float)plane;
   a.lut = pl->lut[0];
+  a.lut_t = pl->lut_t;
   a.n_rings = pl->p.n_rings;
   a.ring_scale = weight;
   a.inv_lx = 1.0 / pl->p.cell[0];

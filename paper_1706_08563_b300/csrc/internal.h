@@ -25,6 +25,7 @@ struct PassArgs {
   const float2* prop_y = nullptr;    // exp(-i pi lambda dz (n/Ly)^2), [N]
   float prop_scale = 1.0f;           // 1/N^2 folds the inverse-FFT normalisation in
   const uint16_t* lut = nullptr;     // [N][N]: bit 15 aperture, bits 0..14 ring or 0x7FFF
+  const uint16_t* lut_t = nullptr;   // the same table transposed, [x][y] (column-wise reads)
   int n_rings = 0;
   float* rings = nullptr;            // [batch][n_rings] (offset to the batch's first wave)
   float ring_scale = 1.0f;
@@ -124,6 +125,7 @@ struct stem_plan_s {
   float2* prop_y = nullptr;
   uint16_t* lut[stem::kMaxLog2F + 1] = {};
   uint16_t* lut_crop[stem::kMaxLog2F + 1] = {};   // window tables W' x W' of the cropped S-matrix
+  uint16_t* lut_t = nullptr;                       // lut[0] transposed (the multislice detector pass)
   int2* beams[stem::kMaxLog2F + 1] = {};
   int n_beams[stem::kMaxLog2F + 1] = {};
   double* beam_turns[stem::kMaxLog2F + 1] = {};   // chi(k_b) / (2 pi) mod 1 per beam

@@ -617,25 +617,24 @@ __global__ void __launch_bounds__(ColTmaCfg<N_>::THREADS, ColTmaCfg<N_>::MINB)
       if (tid == 0 && tile + 2 * gridDim.x < n_tiles) issue(tile + 2 * gridDim.x, b);
       for (int i = tid; i < a.n_rings; i += Cfg::THREADS) ring_acc[i] = 0.0f;
       fft_dist<N, false>(v, view, t, sync, tw);
-      // |Psi_hat|^2 and ring of each pixel, column by column in row order (row
-      // stride S keeps the scattered writes free of bank conflicts); each warp
-      // then sums runs of 32 consecutive rows of one column (warp_run_add)
-      constexpr int S = N + 16 / C;
+      // |Psi_hat|^2 of each pixel, column by column in row order (row stride S
+      // keeps the scattered writes free of bank conflicts); each warp then sums
+      // runs of 32 consecutive rows of one column (warp_run_add), reading their
+      // rings from the transposed table in one contiguous 64-byte load
+      constexpr int S = N + 32 / C;
+      float* pk = reinterpret_cast<float*>(xbuf);
       __syncthreads();
 #pragma unroll
-      for (int q = 0; q < E; ++q) {
-        const int ky = t + q * T;
-        const int r = __ldg(a.lut + (size_t)ky * N + col) & kLutNoRing;
-        xbuf[c * S + ky] = make_float2(cabs2(v[q]), __int_as_float(r));
-      }
+      for (int q = 0; q < E; ++q) pk[c * S + t + q * T] = cabs2(v[q]);
       __syncthreads();
       constexpr int NW = Cfg::THREADS / 32;
       const int lane = tid & 31, warp = tid >> 5;
 #pragma unroll 4
       for (int i = 0; i < E; ++i) {
         const int idx = (warp + NW * i) * 32 + lane;
-        const float2 e = xbuf[(idx / N) * S + idx % N];
-        warp_run_add(ring_acc, __float_as_int(e.y), e.x, kLutNoRing);
+        const int cc = idx / N, row = idx % N;
+        const int r = __ldg(a.lut_t + (size_t)(col0 + cc) * N + row) & kLutNoRing;
+        warp_run_add(ring_acc, r, pk[cc * S + row], kLutNoRing);
       }
       __syncthreads();
       float* out = a.rings + (size_t)wave * a.n_rings;

@@ -10,16 +10,24 @@
 // the real and imaginary parts.  M = 128 pixels, N = 256, K = 16 per
 // tcgen05.mma (kind::f16, FP16 or BF16 in, FP32 accumulate in tensor memory).
 //
-// Per CTA (512 threads, one CTA per SM): all threads stage 64-wide K chunks of
-// A and B into shared memory with cp.async in the 128-byte swizzled K-major
-// layout (more loading warps keep more bytes in flight: 128 -> 256 -> 512
-// threads took a 4096-probe output call at 2048^2 from 9.4 to 7.2 to 6.4 ms);
-// thread 0 issues the MMAs and commits them to an mbarrier per stage; four
-// stages keep the tensor pipe fed.  After the last chunk the warps read the
-// accumulators with tcgen05.ld (a warp may read only the 32 lanes of its
-// quarter, warp mod 4; the warps sharing a quarter split its columns) and
-// scatter the pixels into the probes' windows.  Every wait is bounded (2 s of %globaltimer); on timeout the
-// kernel records STEM_ERR_TIMEOUT in the plan's status word, drains its copies,
+// One persistent CTA per SM, warp-specialised, the roles synchronised by
+// mbarriers only:
+//   warp 0        one thread issues the MMAs of each 64-wide K chunk as soon as
+//                 its stage is full, commits them to the stage's "empty"
+//                 barrier, and after an item's last chunk to the item's
+//                 accumulator barrier;
+//   warps 1 - 11  producers: stage the chunks of A and B into shared memory in
+//                 the 128-byte swizzled K-major layout with cp.async, each
+//                 thread arriving on the stage's "full" barrier when its copies
+//                 land (cp.async.mbarrier.arrive.noinc); four stages;
+//   warps 12 - 15 epilogue: read an item's accumulator with tcgen05.ld (warp w
+//                 reads the lane quarter w mod 4) and scatter the pixels into
+//                 the probes' windows, then release the accumulator.
+// The accumulator is double-buffered in tensor memory (2 x 256 columns), so the
+// MMAs of one item run while the epilogue drains the previous one, and the
+// producers stage the next item's chunks while the current one finishes.
+// Every wait is bounded (2 s of %globaltimer); on timeout the kernel records
+// STEM_ERR_TIMEOUT in the plan's status word, lets its copies and MMAs land,
 // frees its tensor memory and returns.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -32,30 +40,37 @@
 
 namespace stem {
 
-#ifndef STEM_UMMA_THREADS
-#define STEM_UMMA_THREADS 512
-#endif
-constexpr int kUmmaThreads = STEM_UMMA_THREADS;   // 128 or 256: loaders; the epilogue splits columns
-static_assert(kUmmaThreads == 128 || kUmmaThreads == 256 || kUmmaThreads == 512, "4, 8 or 16 warps");
+constexpr int kUmmaThreads = 512;
+constexpr int kProducerWarp0 = 1, kProducerWarps = 11;   // warps 1 .. 11
+constexpr int kProducers = 32 * kProducerWarps;           // 352 threads
+constexpr int kEpilogueWarp0 = 12;                        // warps 12 .. 15 (lane quarters 0 .. 3)
 constexpr int kUmmaStages = 4;
 constexpr int kUmmaGroup = 128;                 // probes per work item (N = 256)
 constexpr int kTileX = 16, kTileY = 8;          // must match prism.cu
 constexpr int kAStage = 128 * 128;              // bytes: 128 rows x 64 halves
 constexpr int kBStage = 256 * 128;              // bytes: 256 rows x 64 halves
 constexpr int kStageBytes = kAStage + kBStage;
-constexpr int kTmemCols = 256;
+constexpr int kAccCols = 256;                   // one accumulator: 128 lanes x 256 FP32 columns
+constexpr int kTmemCols = 2 * kAccCols;         // double-buffered
+constexpr int kACopies = (1024 + kProducers - 1) / kProducers;   // 16-byte copies per producer per chunk
+constexpr int kBCopies = (2048 + kProducers - 1) / kProducers;
 
-size_t umma_smem_bytes() { return (size_t)kUmmaStages * kStageBytes + 1024 + 2048; }
+size_t umma_smem_bytes() { return (size_t)kUmmaStages * kStageBytes + 1024 + 256; }
 int umma_group() { return kUmmaGroup; }
 
 
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, int src_bytes) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+// Arrive on the barrier once this thread's earlier cp.async copies have landed
+// (the barrier's expected count includes this arrival).
+__device__ __forceinline__ void cp_async_arrive(uint32_t bar) {
+  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -148,6 +163,22 @@ __global__ void k_coefficients_umma(const double* __restrict__ xy, const int2* _
   }
 }
 
+// The work item of a CTA's k-th turn: pixel tile and group of its probe list.
+struct UmmaItem {
+  int first, g0, cnt, x0, y0;
+};
+__device__ __forceinline__ UmmaItem umma_item(const int* __restrict__ offsets, const int* __restrict__ work,
+                                              int n_tiles, int ntx, int item) {
+  UmmaItem it;
+  const int tile = find_item_tile(work, n_tiles, item);
+  it.first = __ldg(offsets + tile);
+  it.g0 = (item - __ldg(work + tile)) * kUmmaGroup;
+  it.cnt = min(kUmmaGroup, __ldg(offsets + tile + 1) - it.first - it.g0);
+  it.x0 = (tile % ntx) * kTileX;
+  it.y0 = (tile / ntx) * kTileY;
+  return it;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kUmmaThreads, 1) k_beam_sum_umma(
     const T* __restrict__ sdata, const T* __restrict__ coef, int n, int w, int nbp,
@@ -155,20 +186,29 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_beam_sum_umma(
     const int* __restrict__ list, int n_tiles, float2* __restrict__ windows, int* __restrict__ status) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-  unsigned char* tail = smem + kUmmaStages * kStageBytes;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(tail);                       // kUmmaStages mbarriers
-  uint32_t* s_taddr = reinterpret_cast<uint32_t*>(tail + 64);
-  int* s_abort = reinterpret_cast<int*>(tail + 68);
-  int* s_probe = reinterpret_cast<int*>(tail + 128);                        // kUmmaGroup probe ids
-  int2* s_org = reinterpret_cast<int2*>(tail + 128 + 4 * kUmmaGroup);       // their window origins
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kUmmaStages * kStageBytes);
+  uint64_t* full = bars;                                  // [kUmmaStages]: stage staged
+  uint64_t* empty = bars + kUmmaStages;                   // [kUmmaStages]: stage read by its MMAs
+  uint64_t* acc_full = bars + 2 * kUmmaStages;            // [2]: accumulator complete
+  uint64_t* acc_empty = bars + 2 * kUmmaStages + 2;       // [2]: accumulator read out
+  uint32_t* s_taddr = reinterpret_cast<uint32_t*>(bars + 2 * kUmmaStages + 4);
+  int* s_abort = reinterpret_cast<int*>(s_taddr + 1);
 
-  const int tid = threadIdx.x, warp = tid >> 5;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int K = 2 * nbp, KC = K / 64;
-  const uint32_t idesc = umma_idesc(std::is_same<T, __half>::value ? 0u : 1u);
   const uint32_t sbase = smem_u32(smem);
+  const int total = __ldg(work + n_tiles);
+  const int ntx = n / kTileX;
 
   if (tid == 0) {
-    for (int s = 0; s < kUmmaStages; ++s) mbar_init(smem_u32(bars + s), 1);
+    for (int s = 0; s < kUmmaStages; ++s) {
+      mbar_init(smem_u32(full + s), kProducers);
+      mbar_init(smem_u32(empty + s), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(smem_u32(acc_full + b), 1);
+      mbar_init(smem_u32(acc_empty + b), 4);
+    }
     *s_abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -182,111 +222,117 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_beam_sum_umma(
   __syncthreads();
   tc_fence_after();
   const uint32_t taddr = *s_taddr;
+  auto abort_now = [&] { return *reinterpret_cast<volatile int*>(s_abort) != 0; };
 
-  const int total = __ldg(work + n_tiles);
-  const int ntx = n / kTileX;
-  uint32_t chunk_counter = 0;     // chunks committed so far by this CTA (same on every thread)
-  bool aborted = false;
-
-  for (int item = blockIdx.x; item < total && !aborted; item += gridDim.x) {
-    const int tile = find_item_tile(work, n_tiles, item);
-    const int first = __ldg(offsets + tile);
-    const int g0 = (item - __ldg(work + tile)) * kUmmaGroup;
-    const int cnt = min(kUmmaGroup, __ldg(offsets + tile + 1) - first - g0);
-    const int x0 = (tile % ntx) * kTileX, y0 = (tile / ntx) * kTileY;
-    for (int i = tid; i < kUmmaGroup; i += kUmmaThreads) {
-      const int p = i < cnt ? __ldg(list + first + g0 + i) : -1;
-      s_probe[i] = p;
-      s_org[i] = p >= 0 ? __ldg(origin + p) : make_int2(0, 0);
-    }
-    __syncthreads();
-
-    // loads of one K chunk into stage st: A rows = the tile's pixels, B rows = (probe, re|im)
-    auto load_chunk = [&](int kc, int st) {
-      const uint32_t a_s = sbase + st * kStageBytes, b_s = a_s + kAStage;
-      const int k0 = kc * 64;
-#pragma unroll
-      for (int i = 0; i < 1024 / kUmmaThreads; ++i) {
-        const int idx = tid + i * kUmmaThreads;
-        const int r = idx >> 3, c = idx & 7;
-        const size_t pix = (size_t)(y0 + r / kTileX) * n + x0 + (r % kTileX);
-        cp_async16(a_s + r * 128 + ((c ^ (r & 7)) << 4), sdata + pix * K + k0 + c * 8, 16);
-      }
-#pragma unroll
-      for (int i = 0; i < 2048 / kUmmaThreads; ++i) {
-        const int idx = tid + i * kUmmaThreads;
-        const int r = idx >> 3, c = idx & 7;
-        const int p = s_probe[r >> 1];
-        const T* src = p >= 0 ? coef + ((size_t)p * 2 + (r & 1)) * K + k0 + c * 8 : coef;
-        cp_async16(b_s + r * 128 + ((c ^ (r & 7)) << 4), src, p >= 0 ? 16 : 0);
-      }
-    };
-
-    for (int s = 0; s < kUmmaStages - 1; ++s) {
-      if (s < KC) load_chunk(s, (chunk_counter + s) % kUmmaStages);
-      cp_async_commit();
-    }
-    for (int kc = 0; kc < KC; ++kc) {
-      const uint32_t g = chunk_counter + kc;
-      const int st = g % kUmmaStages;
-      cp_async_wait<kUmmaStages - 2>();
-      fence_proxy_async();
-      __syncthreads();
-      if (tid == 0) {
+  if (warp == 0) {
+    // ---------------------------------------------------------------- MMA issuer
+    if (lane == 0) {
+      const uint32_t idesc = umma_idesc(std::is_same<T, __half>::value ? 0u : 1u);
+      uint32_t g = 0;
+      int it = 0;
+      for (int item = blockIdx.x; item < total; item += gridDim.x, ++it) {
+        const int b = it & 1;
+        if (it >= 2 && !mbar_wait(smem_u32(acc_empty + b), ((it >> 1) - 1) & 1u)) { *s_abort = 1; break; }
         tc_fence_after();
-        const uint32_t a_s = sbase + st * kStageBytes, b_s = a_s + kAStage;
+        const uint32_t acc = taddr + (uint32_t)(b * kAccCols);
+        bool ok = true;
+        for (int kc = 0; kc < KC; ++kc, ++g) {
+          const int st = g % kUmmaStages;
+          if (!mbar_wait(smem_u32(full + st), (g / kUmmaStages) & 1u) || abort_now()) { ok = false; break; }
+          // the producers' cp.async writes (generic proxy) before the MMAs read them (async proxy)
+          fence_proxy_async();
+          tc_fence_after();
+          const uint32_t a_s = sbase + st * kStageBytes, b_s = a_s + kAStage;
 #pragma unroll
-        for (int kk = 0; kk < 4; ++kk)
-          umma_f16(taddr, sw128_desc(a_s + kk * 32), sw128_desc(b_s + kk * 32), idesc, (kc > 0 || kk > 0) ? 1u : 0u);
-        umma_commit(smem_u32(bars + st));
-        // the stage about to be refilled was read by the previous chunk's MMAs
-        if (kc >= 1) {
-          const uint32_t gp = g - 1;
-          if (!mbar_wait(smem_u32(bars + gp % kUmmaStages), (gp / kUmmaStages) & 1u)) *s_abort = 1;
+          for (int kk = 0; kk < 4; ++kk)
+            umma_f16(acc, sw128_desc(a_s + kk * 32), sw128_desc(b_s + kk * 32), idesc, (kc > 0 || kk > 0) ? 1u : 0u);
+          umma_commit(smem_u32(empty + st));
+        }
+        if (!ok) { *s_abort = 1; break; }
+        umma_commit(smem_u32(acc_full + b));
+      }
+      // every MMA issued has landed before the tensor memory is freed
+      if (g > 0) mbar_wait(smem_u32(empty + (g - 1) % kUmmaStages), ((g - 1) / kUmmaStages) & 1u);
+    }
+  } else if (warp < kEpilogueWarp0) {
+    // ---------------------------------------------------------------- producers
+    const int pt = tid - 32 * kProducerWarp0;
+    uint32_t g = 0;
+    for (int item = blockIdx.x; item < total && !abort_now(); item += gridDim.x) {
+      const UmmaItem itm = umma_item(offsets, work, n_tiles, ntx, item);
+      // this thread's copies of every chunk of the item: source rows and swizzled destinations
+      const T* a_src[kACopies];
+      uint32_t a_dst[kACopies];
+#pragma unroll
+      for (int i = 0; i < kACopies; ++i) {
+        const int idx = pt + i * kProducers;
+        const int r = (idx < 1024 ? idx : 0) >> 3, c = idx & 7;
+        const size_t pix = (size_t)(itm.y0 + r / kTileX) * n + itm.x0 + (r % kTileX);
+        a_src[i] = sdata + pix * K + c * 8;
+        a_dst[i] = r * 128 + ((c ^ (r & 7)) << 4);
+      }
+      const T* b_src[kBCopies];
+      uint32_t b_dst[kBCopies];
+      int b_bytes[kBCopies];
+#pragma unroll
+      for (int i = 0; i < kBCopies; ++i) {
+        const int idx = pt + i * kProducers;
+        const int r = (idx < 2048 ? idx : 0) >> 3, c = idx & 7;
+        const int pl = r >> 1;
+        const int p = pl < itm.cnt ? __ldg(list + itm.first + itm.g0 + pl) : -1;
+        b_src[i] = p >= 0 ? coef + ((size_t)p * 2 + (r & 1)) * K + c * 8 : coef;
+        b_bytes[i] = p >= 0 ? 16 : 0;      // probes past the group's count read zeros
+        b_dst[i] = kAStage + r * 128 + ((c ^ (r & 7)) << 4);
+      }
+      bool ok = true;
+      for (int kc = 0; kc < KC; ++kc, ++g) {
+        const int st = g % kUmmaStages;
+        if (g >= kUmmaStages && !mbar_wait(smem_u32(empty + st), ((g / kUmmaStages) - 1) & 1u)) { ok = false; break; }
+        const uint32_t base = sbase + st * kStageBytes;
+        const int k0 = kc * 64;
+#pragma unroll
+        for (int i = 0; i < kACopies; ++i)
+          if (pt + i * kProducers < 1024) cp_async16(base + a_dst[i], a_src[i] + k0, 16);
+#pragma unroll
+        for (int i = 0; i < kBCopies; ++i)
+          if (pt + i * kProducers < 2048) cp_async16(base + b_dst[i], b_src[i] + (b_bytes[i] ? k0 : 0), b_bytes[i]);
+        cp_async_arrive(smem_u32(full + st));
+      }
+      if (!ok) { *s_abort = 1; break; }
+    }
+    cp_async_wait_all();
+  } else {
+    // ---------------------------------------------------------------- epilogue
+    const int quarter = warp % 4;
+    const int r = quarter * 32 + lane;                   // this lane's pixel of the tile
+    int it = 0;
+    for (int item = blockIdx.x; item < total; item += gridDim.x, ++it) {
+      const int b = it & 1;
+      if (!mbar_wait(smem_u32(acc_full + b), (it >> 1) & 1u) || abort_now()) { *s_abort = 1; break; }
+      tc_fence_after();
+      const UmmaItem itm = umma_item(offsets, work, n_tiles, ntx, item);
+      const int gx = itm.x0 + r % kTileX, gy = itm.y0 + r / kTileX;
+      for (int blk = 0; blk < 4; ++blk) {
+        float v[64];
+        tmem_ld64(taddr + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * kAccCols + blk * 64), v);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int pl = blk * 32 + j;
+          if (pl >= itm.cnt) break;
+          const int p = __ldg(list + itm.first + itm.g0 + pl);
+          const int2 o = __ldg(origin + p);
+          const int u = (gx - o.x + n) % n, vv = (gy - o.y + n) % n;
+          if (u < w && vv < w) windows[((size_t)p * w + vv) * w + u] = make_float2(v[2 * j], v[2 * j + 1]);
         }
       }
-      __syncthreads();
-      if (*s_abort) { aborted = true; break; }
-      const int kn = kc + kUmmaStages - 1;
-      if (kn < KC) load_chunk(kn, (chunk_counter + kn) % kUmmaStages);
-      cp_async_commit();
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(acc_empty + b));
     }
-    if (aborted) break;
-    if (tid == 0) {
-      const uint32_t gl = chunk_counter + KC - 1;
-      if (!mbar_wait(smem_u32(bars + gl % kUmmaStages), (gl / kUmmaStages) & 1u)) *s_abort = 1;
-    }
-    chunk_counter += KC;
-    __syncthreads();
-    if (*s_abort) { aborted = true; break; }
-    tc_fence_after();
-
-    // epilogue: lane r of warp w holds pixel 32 (w mod 4) + r of the tile; with
-    // eight warps, warps w and w + 4 share a lane quarter and split its columns
-    constexpr int WARPS = kUmmaThreads / 32, BLKS = 4 / (WARPS / 4);
-    const int quarter = warp % 4;
-    const int r = quarter * 32 + (tid & 31);
-    const int gx = x0 + r % kTileX, gy = y0 + r / kTileX;
-    for (int b = 0; b < BLKS; ++b) {
-      const int blk = (warp / 4) * BLKS + b;
-      float v[64];
-      tmem_ld64(taddr + ((uint32_t)(quarter * 32) << 16) + blk * 64, v);
-#pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        const int pl = blk * 32 + j;
-        const int p = s_probe[pl];
-        if (p < 0) continue;
-        const int2 o = s_org[pl];
-        const int u = (gx - o.x + n) % n, vv = (gy - o.y + n) % n;
-        if (u < w && vv < w) windows[((size_t)p * w + vv) * w + u] = make_float2(v[2 * j], v[2 * j + 1]);
-      }
-    }
-    tc_fence_before();
-    __syncthreads();
   }
 
-  if (aborted && tid == 0) atomicExch(status, (int)STEM_ERR_TIMEOUT);
-  cp_async_wait_all();
+  __syncthreads();
+  if (tid == 0 && *s_abort) atomicExch(status, (int)STEM_ERR_TIMEOUT);
   tc_fence_before();
   __syncthreads();
   if (warp == 0) {

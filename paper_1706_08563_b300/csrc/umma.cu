@@ -55,7 +55,7 @@ constexpr int kTmemCols = 2 * kAccCols;         // double-buffered
 constexpr int kACopies = (1024 + kProducers - 1) / kProducers;   // 16-byte copies per producer per chunk
 constexpr int kBCopies = (2048 + kProducers - 1) / kProducers;
 
-size_t umma_smem_bytes() { return (size_t)kUmmaStages * kStageBytes + 1024 + 256; }
+size_t umma_smem_bytes() { return (size_t)kUmmaStages * kStageBytes + 1024 + 256 + 12 * kUmmaGroup + 16; }
 int umma_group() { return kUmmaGroup; }
 
 
@@ -193,6 +193,9 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_beam_sum_umma(
   uint64_t* acc_empty = bars + 2 * kUmmaStages + 2;       // [2]: accumulator read out
   uint32_t* s_taddr = reinterpret_cast<uint32_t*>(bars + 2 * kUmmaStages + 4);
   int* s_abort = reinterpret_cast<int*>(s_taddr + 1);
+  int* e_flag = s_abort + 1;                                       // epilogue: accumulator ready
+  int2* e_org = reinterpret_cast<int2*>(bars + 2 * kUmmaStages + 6);   // [kUmmaGroup] epilogue's item
+  int* e_probe = reinterpret_cast<int*>(e_org + kUmmaGroup);           // [kUmmaGroup]
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int K = 2 * nbp, KC = K / 64;
@@ -207,7 +210,7 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_beam_sum_umma(
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(smem_u32(acc_full + b), 1);
-      mbar_init(smem_u32(acc_empty + b), 4);
+      mbar_init(smem_u32(acc_empty + b), 1);
     }
     *s_abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -304,13 +307,25 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_beam_sum_umma(
   } else {
     // ---------------------------------------------------------------- epilogue
     const int quarter = warp % 4;
+    const int et = tid - 32 * kEpilogueWarp0;            // 0 .. 127
     const int r = quarter * 32 + lane;                   // this lane's pixel of the tile
+    auto epi_sync = [] { asm volatile("bar.sync 1, 128;" ::: "memory"); };   // the four epilogue warps
     int it = 0;
     for (int item = blockIdx.x; item < total; item += gridDim.x, ++it) {
       const int b = it & 1;
-      if (!mbar_wait(smem_u32(acc_full + b), (it >> 1) & 1u) || abort_now()) { *s_abort = 1; break; }
-      tc_fence_after();
+      // the item's probes and window origins, one per epilogue thread, staged
+      // while its MMAs may still run
       const UmmaItem itm = umma_item(offsets, work, n_tiles, ntx, item);
+      {
+        const int p = et < itm.cnt ? __ldg(list + itm.first + itm.g0 + et) : -1;
+        e_probe[et] = p;
+        e_org[et] = p >= 0 ? __ldg(origin + p) : make_int2(0, 0);
+      }
+      // one thread waits; the named barrier hands all 128 the same verdict
+      if (et == 0) *e_flag = mbar_wait(smem_u32(acc_full + b), (it >> 1) & 1u) && !abort_now();
+      epi_sync();
+      if (!*reinterpret_cast<volatile int*>(e_flag)) { *s_abort = 1; break; }
+      tc_fence_after();
       const int gx = itm.x0 + r % kTileX, gy = itm.y0 + r / kTileX;
       for (int blk = 0; blk < 4; ++blk) {
         float v[64];
@@ -318,16 +333,17 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_beam_sum_umma(
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
           const int pl = blk * 32 + j;
-          if (pl >= itm.cnt) break;
-          const int p = __ldg(list + itm.first + itm.g0 + pl);
-          const int2 o = __ldg(origin + p);
-          const int u = (gx - o.x + n) % n, vv = (gy - o.y + n) % n;
+          const int p = e_probe[pl];
+          if (p < 0) break;
+          const int2 o = e_org[pl];
+          const int du = gx - o.x, dv = gy - o.y;    // in (-n, n): wrap into [0, n)
+          const int u = du < 0 ? du + n : du, vv = dv < 0 ? dv + n : dv;
           if (u < w && vv < w) windows[((size_t)p * w + vv) * w + u] = make_float2(v[2 * j], v[2 * j + 1]);
         }
       }
       tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(smem_u32(acc_empty + b));
+      epi_sync();   // every epilogue thread is done with e_probe / e_org and the accumulator
+      if (et == 0) mbar_arrive(smem_u32(acc_empty + b));
     }
   }
 

@@ -81,7 +81,7 @@ cudaError_t launch_window_fft3(int w, float2* win, int np, const uint16_t* lut, 
                                float* rings, float* dp, int band_w2, cudaStream_t s);
 
 struct OutputWs {
-  size_t coef = 0, origin = 0, counts = 0, offsets = 0, work = 0, list = 0, windows = 0, total = 0;
+  size_t coef = 0, origin = 0, counts = 0, offsets = 0, work = 0, items = 0, list = 0, windows = 0, total = 0;
 };
 OutputWs output_workspace_layout(int n, int f, int chunk, int nbp);
 
@@ -101,9 +101,10 @@ struct OutputArgs {
 // tcgen05 beam sum (umma.cu)
 int umma_group();
 size_t umma_smem_bytes();
+// items[i]: the pixel tile of work item i (items of tile t are work[t] .. work[t+1]-1)
 cudaError_t launch_beam_sum_umma(const OutputArgs& o, int np, const double* probe_xy, void* coef, const int2* origin,
-                                 const int* offsets, const int* work, const int* list, int n_tiles, float2* windows,
-                                 cudaStream_t s);
+                                 const int* offsets, const int* work, const int* items, const int* list, int n_tiles,
+                                 float2* windows, cudaStream_t s);
 
 cudaError_t prism_windows_chunk(const OutputArgs& o, const double* probe_xy, int np, float2* windows,
                                 char* ws, const OutputWs& L, cudaStream_t s);

@@ -157,6 +157,8 @@ OutputWs output_workspace_layout(int n, int f, int chunk, int nbp) {
   L.counts = off;  off += align256(n_tiles * sizeof(int));
   L.offsets = off; off += align256((n_tiles + 1) * sizeof(int));
   L.work = off;    off += align256((n_tiles + 1) * sizeof(int));
+  // items: at most one partial group per tile plus chunk * per_probe / 64 full ones
+  L.items = off;   off += align256((n_tiles + (size_t)chunk * per_probe / 64 + 1) * sizeof(int));
   L.list = off;    off += align256((size_t)chunk * per_probe * sizeof(int));
   L.windows = off; off += align256((size_t)chunk * w * w * sizeof(float2));
   L.total = off;
@@ -252,6 +254,14 @@ __global__ void k_scan_tiles(int* __restrict__ counts, int n_tiles, int group, i
   }
 }
 
+// items[g] = t for every work item g of tile t (a direct look-up instead of a
+// search over the item offsets)
+__global__ void k_item_tiles(const int* __restrict__ work, int n_tiles, int* __restrict__ items) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_tiles) return;
+  for (int g = work[t]; g < work[t + 1]; ++g) items[g] = t;
+}
+
 __global__ void k_fill_tiles(const int2* __restrict__ origin, int np, int n, int w, const int* __restrict__ offsets,
                              int* __restrict__ cursor, int* __restrict__ list) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
@@ -274,20 +284,11 @@ __global__ void k_fill_tiles(const int2* __restrict__ origin, int np, int n, int
 constexpr int kGroup = 64;
 constexpr int kKb = 16;
 
-__device__ __forceinline__ int find_tile(const int* __restrict__ work, int n_tiles, int item) {
-  int lo = 0, hi = n_tiles;          // work[lo] <= item < work[hi]
-  while (hi - lo > 1) {
-    const int mid = (lo + hi) >> 1;
-    if (__ldg(work + mid) <= item) lo = mid; else hi = mid;
-  }
-  return lo;
-}
-
 template <int S>
 __global__ void __launch_bounds__(256) k_beam_sum_simt(
     const typename Elem<S>::T* __restrict__ sdata, int n, int w, int nbp, const float* __restrict__ coef,
     const int2* __restrict__ origin, const int* __restrict__ offsets, const int* __restrict__ work,
-    const int* __restrict__ list, int n_tiles, float2* __restrict__ windows) {
+    const int* __restrict__ items, const int* __restrict__ list, int n_tiles, float2* __restrict__ windows) {
   __shared__ float2 s_sm[kKb][kTilePix];
   __shared__ float2 c_sm[kKb][kGroup];
   __shared__ int p_sm[kGroup];
@@ -296,7 +297,7 @@ __global__ void __launch_bounds__(256) k_beam_sum_simt(
   const int pxg = threadIdx.x & 31;        // pixels 4 pxg .. 4 pxg + 3
   const int prg = threadIdx.x >> 5;        // probes 8 prg .. 8 prg + 7
   for (int item = blockIdx.x; item < total; item += gridDim.x) {
-    const int tile = find_tile(work, n_tiles, item);
+    const int tile = __ldg(items + item);
     const int g0 = (item - __ldg(work + tile)) * kGroup;
     const int first = __ldg(offsets + tile);
     const int cnt = min(kGroup, __ldg(offsets + tile + 1) - first - g0);
@@ -364,6 +365,7 @@ cudaError_t prism_windows_chunk(const OutputArgs& o, const double* probe_xy, int
   int* counts = reinterpret_cast<int*>(ws + L.counts);
   int* offsets = reinterpret_cast<int*>(ws + L.offsets);
   int* work = reinterpret_cast<int*>(ws + L.work);
+  int* items = reinterpret_cast<int*>(ws + L.items);
   int* list = reinterpret_cast<int*>(ws + L.list);
   const int n = o.n, w = o.w;
   const int n_tiles = (n / kTileX) * (n / kTileY);
@@ -384,8 +386,11 @@ cudaError_t prism_windows_chunk(const OutputArgs& o, const double* probe_xy, int
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   note_launch(), k_fill_tiles<<<(np + 127) / 128, 128, 0, s>>>(origin, np, n, w, offsets, counts, list);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  note_launch(), k_item_tiles<<<(n_tiles + 255) / 256, 256, 0, s>>>(work, n_tiles, items);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
 
-  if (tensor) return launch_beam_sum_umma(o, np, probe_xy, coef, origin, offsets, work, list, n_tiles, windows, s);
+  if (tensor)
+    return launch_beam_sum_umma(o, np, probe_xy, coef, origin, offsets, work, items, list, n_tiles, windows, s);
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -393,15 +398,15 @@ cudaError_t prism_windows_chunk(const OutputArgs& o, const double* probe_xy, int
   switch (o.storage) {
     case STEM_F32:
       note_launch(), k_beam_sum_simt<STEM_F32><<<grid, 256, 0, s>>>(static_cast<const float*>(o.sdata), n, w, o.nbp, coef, origin,
-                                                     offsets, work, list, n_tiles, windows);
+                                                     offsets, work, items, list, n_tiles, windows);
       break;
     case STEM_F16:
       note_launch(), k_beam_sum_simt<STEM_F16><<<grid, 256, 0, s>>>(static_cast<const __half*>(o.sdata), n, w, o.nbp, coef, origin,
-                                                     offsets, work, list, n_tiles, windows);
+                                                     offsets, work, items, list, n_tiles, windows);
       break;
     case STEM_BF16:
       note_launch(), k_beam_sum_simt<STEM_BF16><<<grid, 256, 0, s>>>(static_cast<const __nv_bfloat16*>(o.sdata), n, w, o.nbp, coef,
-                                                      origin, offsets, work, list, n_tiles, windows);
+                                                      origin, offsets, work, items, list, n_tiles, windows);
       break;
     default: return cudaErrorInvalidValue;
   }

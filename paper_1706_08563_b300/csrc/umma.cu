@@ -122,15 +122,6 @@ __device__ __forceinline__ void tmem_ld64(uint32_t taddr, float (&r)[64]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-__device__ __forceinline__ int find_item_tile(const int* __restrict__ work, int n_tiles, int item) {
-  int lo = 0, hi = n_tiles;
-  while (hi - lo > 1) {
-    const int mid = (lo + hi) >> 1;
-    if (__ldg(work + mid) <= item) lo = mid; else hi = mid;
-  }
-  return lo;
-}
-
 // Coefficients as the B operand: row (p, h) of length K = 2 nbp, 16-bit.
 template <typename T>
 __global__ void k_coefficients_umma(const double* __restrict__ xy, const int2* __restrict__ beams,
@@ -168,9 +159,9 @@ struct UmmaItem {
   int first, g0, cnt, x0, y0;
 };
 __device__ __forceinline__ UmmaItem umma_item(const int* __restrict__ offsets, const int* __restrict__ work,
-                                              int n_tiles, int ntx, int item) {
+                                              const int* __restrict__ items, int ntx, int item) {
   UmmaItem it;
-  const int tile = find_item_tile(work, n_tiles, item);
+  const int tile = __ldg(items + item);
   it.first = __ldg(offsets + tile);
   it.g0 = (item - __ldg(work + tile)) * kUmmaGroup;
   it.cnt = min(kUmmaGroup, __ldg(offsets + tile + 1) - it.first - it.g0);
@@ -183,7 +174,8 @@ template <typename T>
 __global__ void __launch_bounds__(kUmmaThreads, 1) k_beam_sum_umma(
     const T* __restrict__ sdata, const T* __restrict__ coef, int n, int w, int nbp,
     const int2* __restrict__ origin, const int* __restrict__ offsets, const int* __restrict__ work,
-    const int* __restrict__ list, int n_tiles, float2* __restrict__ windows, int* __restrict__ status) {
+    const int* __restrict__ items, const int* __restrict__ list, int n_tiles, float2* __restrict__ windows,
+    int* __restrict__ status) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kUmmaStages * kStageBytes);
@@ -260,9 +252,25 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_beam_sum_umma(
   } else if (warp < kEpilogueWarp0) {
     // ---------------------------------------------------------------- producers
     const int pt = tid - 32 * kProducerWarp0;
+    // the probe ids of this thread's B rows for an item (loads issued one item
+    // ahead, so that their latency hides behind the chunks of the current item)
+    auto probe_ids = [&](const UmmaItem& itm, int (&pid)[kBCopies]) {
+#pragma unroll
+      for (int i = 0; i < kBCopies; ++i) {
+        const int idx = pt + i * kProducers;
+        const int pl = ((idx < 2048 ? idx : 0) >> 3) >> 1;
+        pid[i] = pl < itm.cnt ? __ldg(list + itm.first + itm.g0 + pl) : -1;
+      }
+    };
     uint32_t g = 0;
-    for (int item = blockIdx.x; item < total && !abort_now(); item += gridDim.x) {
-      const UmmaItem itm = umma_item(offsets, work, n_tiles, ntx, item);
+    int item = blockIdx.x;
+    UmmaItem itm{};
+    int pid[kBCopies];
+    if (item < total) {
+      itm = umma_item(offsets, work, items, ntx, item);
+      probe_ids(itm, pid);
+    }
+    for (; item < total && !abort_now(); item += gridDim.x) {
       // this thread's copies of every chunk of the item: source rows and swizzled destinations
       const T* a_src[kACopies];
       uint32_t a_dst[kACopies];
@@ -276,16 +284,18 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_beam_sum_umma(
       }
       const T* b_src[kBCopies];
       uint32_t b_dst[kBCopies];
-      int b_bytes[kBCopies];
 #pragma unroll
       for (int i = 0; i < kBCopies; ++i) {
         const int idx = pt + i * kProducers;
         const int r = (idx < 2048 ? idx : 0) >> 3, c = idx & 7;
-        const int pl = r >> 1;
-        const int p = pl < itm.cnt ? __ldg(list + itm.first + itm.g0 + pl) : -1;
-        b_src[i] = p >= 0 ? coef + ((size_t)p * 2 + (r & 1)) * K + c * 8 : coef;
-        b_bytes[i] = p >= 0 ? 16 : 0;      // probes past the group's count read zeros
+        b_src[i] = pid[i] >= 0 ? coef + ((size_t)pid[i] * 2 + (r & 1)) * K + c * 8 : nullptr;
         b_dst[i] = kAStage + r * 128 + ((c ^ (r & 7)) << 4);
+      }
+      // the next item's tile and probe ids, in flight while this item's chunks stream
+      const int next = item + gridDim.x;
+      if (next < total) {
+        itm = umma_item(offsets, work, items, ntx, next);
+        probe_ids(itm, pid);
       }
       bool ok = true;
       for (int kc = 0; kc < KC; ++kc, ++g) {
@@ -298,7 +308,11 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_beam_sum_umma(
           if (pt + i * kProducers < 1024) cp_async16(base + a_dst[i], a_src[i] + k0, 16);
 #pragma unroll
         for (int i = 0; i < kBCopies; ++i)
-          if (pt + i * kProducers < 2048) cp_async16(base + b_dst[i], b_src[i] + (b_bytes[i] ? k0 : 0), b_bytes[i]);
+          if (pt + i * kProducers < 2048) {
+            // probes past the group's count read zeros (a zero-byte copy from any valid address)
+            if (b_src[i]) cp_async16(base + b_dst[i], b_src[i] + k0, 16);
+            else cp_async16(base + b_dst[i], coef, 0);
+          }
         cp_async_arrive(smem_u32(full + st));
       }
       if (!ok) { *s_abort = 1; break; }
@@ -315,7 +329,7 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_beam_sum_umma(
       const int b = it & 1;
       // the item's probes and window origins, one per epilogue thread, staged
       // while its MMAs may still run
-      const UmmaItem itm = umma_item(offsets, work, n_tiles, ntx, item);
+      const UmmaItem itm = umma_item(offsets, work, items, ntx, item);
       {
         const int p = et < itm.cnt ? __ldg(list + itm.first + itm.g0 + et) : -1;
         e_probe[et] = p;
@@ -358,8 +372,8 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_beam_sum_umma(
 }
 
 cudaError_t launch_beam_sum_umma(const OutputArgs& o, int np, const double* probe_xy, void* coef,
-                                 const int2* origin, const int* offsets, const int* work, const int* list,
-                                 int n_tiles, float2* windows, cudaStream_t s) {
+                                 const int2* origin, const int* offsets, const int* work, const int* items,
+                                 const int* list, int n_tiles, float2* windows, cudaStream_t s) {
   const double inv_lx = 1.0 / o.lx, inv_ly = 1.0 / o.ly;
   dim3 cg((o.nbp + 127) / 128, np);
   int dev = 0, sms = 148;
@@ -375,7 +389,7 @@ cudaError_t launch_beam_sum_umma(const OutputArgs& o, int np, const double* prob
       return e;
     note_launch(), k_beam_sum_umma<__half><<<sms, kUmmaThreads, smem, s>>>(
         static_cast<const __half*>(o.sdata), static_cast<const __half*>(coef), o.n, o.w, o.nbp, origin, offsets,
-        work, list, n_tiles, windows, o.status);
+        work, items, list, n_tiles, windows, o.status);
   } else if (o.storage == STEM_BF16) {
     note_launch(), k_coefficients_umma<__nv_bfloat16><<<cg, 128, 0, s>>>(
         probe_xy, o.beams, o.beam_turns, o.n_beams, o.nbp, o.scales, inv_lx, inv_ly, o.coef_norm,
@@ -385,7 +399,7 @@ cudaError_t launch_beam_sum_umma(const OutputArgs& o, int np, const double* prob
       return e;
     note_launch(), k_beam_sum_umma<__nv_bfloat16><<<sms, kUmmaThreads, smem, s>>>(
         static_cast<const __nv_bfloat16*>(o.sdata), static_cast<const __nv_bfloat16*>(coef), o.n, o.w, o.nbp,
-        origin, offsets, work, list, n_tiles, windows, o.status);
+        origin, offsets, work, items, list, n_tiles, windows, o.status);
   } else {
     return cudaErrorInvalidValue;
   }

@@ -14,6 +14,8 @@ Cases
   smat2048  S-matrix, 2048^2, f=8, FP16 storage, 2 slices (793 beams, batches of 128)
   out2048   PRISM f=8 output for 4096 probes from a 2-slice S-matrix (FP16)
   smat2048c, out2048c  the same with the Fourier-cropped S-matrix (1536^2, windows of 192)
+  pot2048   projected potentials and transmission functions of the full PRISM f=8 bench
+            specimen (50 000 atoms, 100 slices of 2048^2)  -> k_potential
 """
 from __future__ import annotations
 
@@ -31,7 +33,7 @@ import torch  # noqa: E402
 import workloads as W  # noqa: E402
 from paper_1706_08563_b300 import api  # noqa: E402
 
-CASES = ("ms2048", "ms1024", "smat2048", "out2048", "smat2048c", "out2048c")
+CASES = ("ms2048", "ms1024", "smat2048", "out2048", "smat2048c", "out2048c", "pot2048")
 
 
 def _timed(fn, repeat):
@@ -49,6 +51,16 @@ def _timed(fn, repeat):
 
 def run(case: str, repeat: int = 1) -> dict:
     dev = torch.device("cuda", torch.cuda.current_device())
+    if case == "pot2048":
+        w = W.C4
+        xyz, gauss = W.atoms(w)
+        plan = api.Plan.from_workload(w, device=dev)
+        d_xyz, d_gauss = torch.from_numpy(xyz).to(dev), torch.from_numpy(gauss).to(dev)
+        out = torch.empty((w.n_slices, w.n, w.n), dtype=torch.complex64, device=dev)
+        ws = plan.potentials_workspace(w.n_atoms)
+        return {"case": case, "grid": w.n, "slices": w.n_slices, "atoms": w.n_atoms,
+                "ms_per_call": _timed(lambda: plan.slice_potentials(d_xyz, d_gauss, out=out, workspace=ws),
+                                      repeat)}
     if case in ("ms2048", "smat2048", "out2048", "smat2048c", "out2048c"):
         base = W.C4
         slices = 4 if case == "ms2048" else 2

@@ -57,6 +57,18 @@ def test_potentials_vs_oracle(api):
     assert np.max(np.abs(trans.cpu().numpy() - tref)) <= 2e-6
 
 
+def test_potentials_repeatable(api):
+    """The FP32 sums run in an order fixed by the input: two calls agree bit for bit."""
+    w = W.scaled(W.C2, n_atoms=2000)
+    xyz, gauss = W.atoms(w, seed=12)
+    plan = api.Plan.from_workload(w)
+    _, v1 = plan.slice_potentials(dev(xyz), dev(gauss), want_v=True)
+    _, v2 = plan.slice_potentials(dev(xyz), dev(gauss), want_v=True)
+    assert torch.equal(v1, v2)
+    vref = O.projected_potential(O.params_from(w), xyz, gauss)
+    assert np.max(np.abs(v1.cpu().numpy() - vref)) <= 2e-6 * np.max(vref)
+
+
 # ------------------------------------------------------------------ detector
 def test_detector_readout_vs_oracle(api):
     w = W.scaled(W.C1, n=64)

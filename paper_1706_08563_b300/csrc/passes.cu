@@ -518,16 +518,22 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, ColCfg<N>::MINB) k_col_pas
 // ---------------------------------------------------------------------------
 // Slice-loop column pass of the large transforms (N = 1024, 2048) moved by the
 // tensor memory accelerator.  A tile (C = 4 columns x N rows, 64 KB at 2048)
-// reaches shared memory as N / 256 2D tensor copies of 256 rows issued by one
-// thread, one tile ahead of the transform (two buffers, one mbarrier each),
-// and leaves it the same way: the transformed tile is written back into its
-// buffer and stored by N / 256 bulk tensor copies, after which the buffer
-// takes the tile after next.  The threads issue no global loads or stores for
-// the wave.  Every mbarrier wait is bounded; on timeout the kernel records
-// STEM_ERR_TIMEOUT in the status word, waits (bounded) for its copies in
-// flight and returns.  The detector variant (DET), the last pass of a
-// multislice run, loads tiles the same way, squares the forward transform and
-// sums it into the rings instead of storing anything.
+// reaches shared memory as N / 256 2D tensor copies of 256 rows, one tile
+// ahead of the transform (two buffers, one "full" mbarrier each), and leaves
+// it the same way: the transformed tile is written back into its buffer and
+// stored by N / 256 bulk tensor copies, after which the buffer takes the tile
+// after next.  The slice pass is warp-specialised: C x T transform threads
+// (synchronised among themselves by named barrier 1) and one copy warp whose
+// lane 0 issues every tensor copy.  When the transform threads have written a
+// tile back they arrive on the buffer's "done" mbarrier; the copy thread
+// stores the tile, waits until the store has read the buffer and refills it,
+// while the transform threads go on with the other buffer.  The threads issue
+// no global loads or stores for the wave.  Every mbarrier wait is bounded; on
+// timeout the kernel records STEM_ERR_TIMEOUT in the status word, waits
+// (bounded) for its copies in flight and returns.  The detector variant (DET),
+// the last pass of a multislice run, loads tiles the same way (all its threads
+// compute; thread 0 issues the copies), squares the forward transform and sums
+// it into the rings instead of storing anything.
 // ---------------------------------------------------------------------------
 #ifndef STEM_COL_TMA_MINB_1024
 #define STEM_COL_TMA_MINB_1024 2
@@ -550,24 +556,29 @@ template <int N_> struct ColTmaCfg {
   static constexpr int LO = (MB + 1 + C - 1) / C, HI0 = (N - MB) / C;
   static constexpr int BAND_TILES = LO + N / C - HI0;
   __device__ static int band_tile(int k) { return k >= LO ? k - LO + HI0 : k; }
+  // threads per CTA: the slice pass adds the copy warp
+  static constexpr int threads(bool det) { return det ? THREADS : THREADS + 32; }
 };
 
 template <int N_, bool DET>
-__global__ void __launch_bounds__(ColTmaCfg<N_>::THREADS, ColTmaCfg<N_>::MINB)
+__global__ void __launch_bounds__(ColTmaCfg<N_>::threads(DET), ColTmaCfg<N_>::MINB)
     k_col_slice_tma(const PassArgs a, const __grid_constant__ CUtensorMap map, int n_tiles) {
   using Cfg = ColTmaCfg<N_>;
   constexpr int N = Cfg::N, E = Cfg::E, T = Cfg::T, C = Cfg::C;
+  constexpr int NT = Cfg::THREADS;   // transform threads
   extern __shared__ unsigned char smem_raw[];
   unsigned char* base = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
   float2* stage = reinterpret_cast<float2*>(base);                        // [2][N][C]
   float2* xbuf = reinterpret_cast<float2*>(base + 2 * (size_t)Cfg::STAGE_BYTES);
   float2* tw = reinterpret_cast<float2*>(reinterpret_cast<unsigned char*>(xbuf) + Cfg::XBUF);
   uint64_t* bars = reinterpret_cast<uint64_t*>(reinterpret_cast<unsigned char*>(tw) + Cfg::TW);
+  // bars[0..1]: buffer full (tensor load landed); bars[2..3]: buffer done
+  // (transformed tile written back; slice pass); bars[4] (an int): abort flag
+  int* s_abort = reinterpret_cast<int*>(bars + 4);
   float* ring_acc = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(bars) + 64);   // DET only
   const int tid = threadIdx.x;
-  const int c = tid % C, t = tid / C;
+  const int c = tid % C, t = (tid / C) % T;
   const SmemView<E, C> view{xbuf + c};
-  auto sync = [] { __syncthreads(); };
 
   auto issue = [&](int tile, int b) {
     const int wave = tile / Cfg::BAND_TILES;
@@ -581,41 +592,112 @@ __global__ void __launch_bounds__(ColTmaCfg<N_>::THREADS, ColTmaCfg<N_>::MINB)
   };
 
   if (tid == 0) {
-    mbar_init(smem_u32(bars), 1);
-    mbar_init(smem_u32(bars + 1), 1);
+    for (int i = 0; i < 4; ++i) mbar_init(smem_u32(bars + i), 1);
+    *s_abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  build_twiddles<N>(tw, tid, Cfg::THREADS);
+  build_twiddles<N>(tw, tid, Cfg::threads(DET));
   __syncthreads();
-  if (tid == 0) {
+  // the copy thread: thread 0 of the detector variant, lane 0 of the copy warp otherwise
+  const bool copier = DET ? tid == 0 : tid == NT;
+  if (copier) {
     if (blockIdx.x < n_tiles) issue(blockIdx.x, 0);
     if (blockIdx.x + gridDim.x < n_tiles) issue(blockIdx.x + gridDim.x, 1);
   }
 
-  int k = 0;
-  bool aborted = false;
-  for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++k) {
-    const int b = k & 1;
-    const bool ok = mbar_wait(smem_u32(bars + b), (uint32_t)(k >> 1) & 1u);
-    if (__syncthreads_or(!ok)) {
-      aborted = true;
-      break;
-    }
-    float2* st = stage + (size_t)b * N * C;
-    float2 v[E];
+  if constexpr (!DET) {
+    if (tid >= NT) {
+      // ------------------------------------------------------------ copy warp
+      if (tid == NT) {
+        int k = 0;
+        bool failed = false;
+        for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++k) {
+          const int b = k & 1;
+          if (!mbar_wait(smem_u32(bars + 2 + b), (uint32_t)(k >> 1) & 1u)) { failed = true; break; }
+          if (*reinterpret_cast<volatile int*>(s_abort)) { failed = true; break; }
+          const int wave = tile / Cfg::BAND_TILES;
+          const int col0 = Cfg::band_tile(tile % Cfg::BAND_TILES) * C;
+          const uint32_t src = smem_u32(stage + (size_t)b * N * C);
 #pragma unroll
-    for (int q = 0; q < E; ++q) v[q] = st[(t + q * T) * C + c];
-
-    const int wave = tile / Cfg::BAND_TILES;
-    const int col0 = Cfg::band_tile(tile % Cfg::BAND_TILES) * C;
-    const int col = col0 + c;
-    if constexpr (DET) {
-      // detector pass: nothing is stored back, so the buffer takes the tile
-      // after next as soon as every thread holds its values; the rings of the
-      // previous tile have been flushed, so they can be cleared
+          for (int y = 0; y < Cfg::BOXES; ++y)
+            tma_store_3d(&map, 2 * col0, y * Cfg::BOX_ROWS, wave, src + y * Cfg::BOX_BYTES);
+          bulk_commit();
+          if (tile + 2 * gridDim.x < n_tiles) {
+            bulk_wait_read();   // buffer b is read out: refill it with the tile after next
+            issue(tile + 2 * gridDim.x, b);
+          }
+        }
+        bulk_wait_all();
+        if (failed) {
+          if (a.status) atomicExch(a.status, (int)STEM_ERR_TIMEOUT);
+          // let the loads already issued into this CTA's buffers land before it
+          // exits: tiles k and k + 1 may still be in flight
+          int tile = blockIdx.x + k * gridDim.x;
+          for (int j = 0; j < 2 && tile < n_tiles; ++j, ++k, tile += gridDim.x)
+            mbar_wait(smem_u32(bars + (k & 1)), (uint32_t)(k >> 1) & 1u);
+        }
+      }
+      return;
+    }
+    // -------------------------------------------------------- transform threads
+    auto sync = [] { named_sync(1, NT); };
+    int k = 0;
+    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++k) {
+      const int b = k & 1;
+      const bool ok = mbar_wait(smem_u32(bars + b), (uint32_t)(k >> 1) & 1u);
+      if (named_sync_or(1, NT, !ok)) {
+        // hand the verdict to the copy thread, which records it and drains
+        if (tid == 0) {
+          *s_abort = 1;
+          mbar_arrive_one(smem_u32(bars + 2 + b));
+        }
+        break;
+      }
+      float2* st = stage + (size_t)b * N * C;
+      float2 v[E];
+#pragma unroll
+      for (int q = 0; q < E; ++q) v[q] = st[(t + q * T) * C + c];
+      const int col = Cfg::band_tile(tile % Cfg::BAND_TILES) * C + c;
+      fft_dist<N, false>(v, view, t, sync, tw);
+      const int m = signed_freq(col, N);
+      const float2 px = cscale(__ldg(a.prop_x + col), a.prop_scale);
+#pragma unroll
+      for (int q = 0; q < E; ++q) {
+        const int ky = t + q * T;
+        const int n = signed_freq(ky, N);
+        const bool keep = !all_out_of_band<N, T>(q) && 9 * (m * m + n * n) <= N * N;
+        v[q] = keep ? cmul(v[q], cmul(px, __ldg(a.prop_y + ky))) : make_float2(0.0f, 0.0f);
+      }
+      fft_dist<N, true>(v, view, t, sync, tw);
+#pragma unroll
+      for (int q = 0; q < E; ++q) st[(t + q * T) * C + c] = v[q];
+      fence_proxy_async();   // these writes before the tensor store reads them
+      sync();                // ... by every transform thread; also frees xbuf for the next tile
+      if (tid == 0) mbar_arrive_one(smem_u32(bars + 2 + b));
+    }
+  } else {
+    auto sync = [] { __syncthreads(); };
+    int k = 0;
+    bool aborted = false;
+    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++k) {
+      const int b = k & 1;
+      const bool ok = mbar_wait(smem_u32(bars + b), (uint32_t)(k >> 1) & 1u);
+      if (__syncthreads_or(!ok)) {
+        aborted = true;
+        break;
+      }
+      float2* st = stage + (size_t)b * N * C;
+      float2 v[E];
+#pragma unroll
+      for (int q = 0; q < E; ++q) v[q] = st[(t + q * T) * C + c];
+      const int wave = tile / Cfg::BAND_TILES;
+      const int col0 = Cfg::band_tile(tile % Cfg::BAND_TILES) * C;
+      // nothing is stored back, so the buffer takes the tile after next as
+      // soon as every thread holds its values; the rings of the previous tile
+      // have been flushed, so they can be cleared
       __syncthreads();
       if (tid == 0 && tile + 2 * gridDim.x < n_tiles) issue(tile + 2 * gridDim.x, b);
-      for (int i = tid; i < a.n_rings; i += Cfg::THREADS) ring_acc[i] = 0.0f;
+      for (int i = tid; i < a.n_rings; i += NT) ring_acc[i] = 0.0f;
       fft_dist<N, false>(v, view, t, sync, tw);
       // |Psi_hat|^2 of each pixel, column by column in row order (row stride S
       // keeps the scattered writes free of bank conflicts); each warp then sums
@@ -627,7 +709,7 @@ __global__ void __launch_bounds__(ColTmaCfg<N_>::THREADS, ColTmaCfg<N_>::MINB)
 #pragma unroll
       for (int q = 0; q < E; ++q) pk[c * S + t + q * T] = cabs2(v[q]);
       __syncthreads();
-      constexpr int NW = Cfg::THREADS / 32;
+      constexpr int NW = NT / 32;
       const int lane = tid & 31, warp = tid >> 5;
 #pragma unroll 4
       for (int i = 0; i < E; ++i) {
@@ -638,46 +720,18 @@ __global__ void __launch_bounds__(ColTmaCfg<N_>::THREADS, ColTmaCfg<N_>::MINB)
       }
       __syncthreads();
       float* out = a.rings + (size_t)wave * a.n_rings;
-      for (int i = tid; i < a.n_rings; i += Cfg::THREADS) {
+      for (int i = tid; i < a.n_rings; i += NT) {
         const float acc = ring_acc[i];
         if (acc != 0.0f) atomicAdd(out + i, acc * a.ring_scale);
       }
-      continue;
     }
-    fft_dist<N, false>(v, view, t, sync, tw);
-    const int m = signed_freq(col, N);
-    const float2 px = cscale(__ldg(a.prop_x + col), a.prop_scale);
-#pragma unroll
-    for (int q = 0; q < E; ++q) {
-      const int ky = t + q * T;
-      const int n = signed_freq(ky, N);
-      const bool keep = !all_out_of_band<N, T>(q) && 9 * (m * m + n * n) <= N * N;
-      v[q] = keep ? cmul(v[q], cmul(px, __ldg(a.prop_y + ky))) : make_float2(0.0f, 0.0f);
+    if (aborted && tid == 0) {
+      if (a.status) atomicExch(a.status, (int)STEM_ERR_TIMEOUT);
+      // let the copies already issued into this CTA's buffers land before it exits
+      int tile = blockIdx.x + k * gridDim.x;
+      for (int j = 0; j < 2 && tile < n_tiles; ++j, ++k, tile += gridDim.x)
+        mbar_wait(smem_u32(bars + (k & 1)), (uint32_t)(k >> 1) & 1u);
     }
-    fft_dist<N, true>(v, view, t, sync, tw);
-#pragma unroll
-    for (int q = 0; q < E; ++q) st[(t + q * T) * C + c] = v[q];
-    fence_proxy_async();   // these writes before the tensor store reads them
-    __syncthreads();
-    if (tid == 0) {
-      const uint32_t src = smem_u32(st);
-#pragma unroll
-      for (int y = 0; y < Cfg::BOXES; ++y) tma_store_3d(&map, 2 * col0, y * Cfg::BOX_ROWS, wave, src + y * Cfg::BOX_BYTES);
-      bulk_commit();
-      if (tile + 2 * gridDim.x < n_tiles) {
-        bulk_wait_read();   // buffer b is read out: refill it with the tile after next
-        issue(tile + 2 * gridDim.x, b);
-      }
-    }
-  }
-  if (!DET && tid == 0) bulk_wait_all();
-
-  if (aborted && tid == 0) {
-    if (a.status) atomicExch(a.status, (int)STEM_ERR_TIMEOUT);
-    // let the copies already issued into this CTA's buffers land before it exits
-    int tile = blockIdx.x + k * gridDim.x;
-    for (int j = 0; j < 2 && tile < n_tiles; ++j, ++k, tile += gridDim.x)
-      mbar_wait(smem_u32(bars + (k & 1)), (uint32_t)(k >> 1) & 1u);
   }
 }
 
@@ -826,12 +880,12 @@ static cudaError_t col_slice_tma(const PassArgs& a, cudaStream_t s) {
     int dev = 0, sms = 148, per = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_col_slice_tma<N, DET>, Cfg::THREADS, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_col_slice_tma<N, DET>, Cfg::threads(DET), smem);
     grid = std::min(n_tiles, sms * std::max(per, 1));
   } else {
-    grid = std::min(n_tiles, resident_ctas(k_col_slice_tma<N, DET>, Cfg::THREADS, smem, occ_flag, occ));
+    grid = std::min(n_tiles, resident_ctas(k_col_slice_tma<N, DET>, Cfg::threads(DET), smem, occ_flag, occ));
   }
-  note_launch(), k_col_slice_tma<N, DET><<<grid, Cfg::THREADS, smem, s>>>(a, map, n_tiles);
+  note_launch(), k_col_slice_tma<N, DET><<<grid, Cfg::threads(DET), smem, s>>>(a, map, n_tiles);
   return cudaGetLastError();
 }
 

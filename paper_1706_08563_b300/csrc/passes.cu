@@ -240,62 +240,114 @@ __global__ void __launch_bounds__(RowCfg<N>::THREADS, RowCfg<N>::MINB) k_row_pas
 // ---------------------------------------------------------------------------
 // Slice row pass at N = 2048 on pairs of waves: a tile is one row of two
 // neighbouring waves, transformed together (fft_dist_x2) against one staged
-// row of t_n.
+// row of t_n.  The in-band part of the tile's two rows (x in [0, 684) and
+// [1364, 2048): two 5 472-byte bulk copies per row) reaches shared memory one
+// tile ahead: thread 0 issues the next tile's copies as soon as every thread
+// has taken the current tile into registers, so the transform never waits on
+// a global load.  The stage-2 twiddles live in registers (computed once per
+// CTA), which leaves room in shared memory for the row stage at three CTAs
+// per SM.
 // ---------------------------------------------------------------------------
-#ifndef STEM_ROW_PAIR
-#define STEM_ROW_PAIR 1
-#endif
-// Stage-1 / stage-2 twiddles of the pair's transforms held in registers.  A
-// thread's butterflies have the same twiddles in every tile, so the stage-2
-// ones (14 complex values) are loaded once per CTA: 164 registers, still three
-// CTAs per SM (the register bound of __launch_bounds__(128, 3) would force 168
-// and spill), 1.3% off the slice loop at 2048; the stage-1 ones as well would
-// leave two CTAs per SM (no gain).
-#ifndef STEM_ROW_PAIR_TW1
-#define STEM_ROW_PAIR_TW1 0
-#endif
-#ifndef STEM_ROW_PAIR_TW2
-#define STEM_ROW_PAIR_TW2 1
-#endif
-#ifndef STEM_ROW_PAIR_MINB
-#define STEM_ROW_PAIR_MINB (STEM_ROW_PAIR_TW2 ? 2 : 3)
-#endif
+// Stage-2 twiddles of the pair's transforms held in registers: a thread's
+// butterflies have the same twiddles in every tile, so the 14 complex values
+// are computed once per CTA: 164 registers, three CTAs per SM (the register
+// bound of __launch_bounds__(128, 3) would force 168 and spill), 1.3% off the
+// slice loop at 2048; the stage-1 ones as well would leave two CTAs per SM
+// (no gain).
 struct RowPairCfg {
   static constexpr int N = 2048, E = FftShape<N>::E, T = N / E, THREADS = T;
   static constexpr int ROWBUF = N + N / E;
-  static constexpr size_t SMEM = ((size_t)2 * ROWBUF + TwLayout<N>::TOTAL + N) * sizeof(float2) + 16;
+  // in-band segments of a row, widened to 16-byte multiples: [0, SEG) and [N - SEG, N)
+  static constexpr int SEG = ((N / 3 + 1) + 1) & ~1;                 // 684
+  static constexpr uint32_t SEG_BYTES = SEG * sizeof(float2);         // 5 472
+  static constexpr int TW1 = TwLayout<N>::SIZE1;                      // stage-1 table in shared memory
+  static constexpr size_t SMEM =
+      ((size_t)2 * ROWBUF + TW1 + N + 2 * 2 * SEG) * sizeof(float2) + 2 * sizeof(uint64_t);
+  static_assert(SEG_BYTES % 16 == 0 && ((N - SEG) * sizeof(float2)) % 16 == 0, "bulk copy alignment");
+  static_assert(((2 * ROWBUF + TW1) * sizeof(float2)) % 16 == 0, "t_n row buffer alignment");
+  // shared-memory slot of in-band element x of a staged row
+  __device__ static int seg_slot(int x) { return x < SEG ? x : x - (N - 2 * SEG); }
 };
 
-__global__ void __launch_bounds__(RowPairCfg::THREADS, STEM_ROW_PAIR_MINB)
-    k_row_slice_pair_2048(const PassArgs a, int n_tiles) {
+// The stage-1 part of build_twiddles<2048> (the stage-2 twiddles are computed
+// into registers by row_pair_stage2_twiddles).
+__device__ __forceinline__ void build_twiddles_stage1(float2* tw, int tid, int nthreads) {
+  using L = TwLayout<2048>;
+  for (int i = tid; i < L::SIZE1; i += nthreads) {
+    const int r = i / L::NS1 + 1, q = i % L::NS1, len = L::NS1 * L::R1;
+    const int p = (r * q) % len;
+    float sn, cs;
+    sincospif(-2.0f * (float)p / (float)len, &sn, &cs);
+    tw[i] = make_float2(cs, sn);
+  }
+}
+
+// The values load_stage_twiddles would read from a full table, computed the
+// way build_twiddles computes them (bit for bit).
+__device__ __forceinline__ void row_pair_stage2_twiddles(StageTwiddles<2048>& reg, int t) {
+  using S = FftShape<2048>;
+  using L = TwLayout<2048>;
+  constexpr int E = S::E, R = S::R2, NS = L::NS2, T = 2048 / E, len = NS * R;
+#pragma unroll
+  for (int i = 0; i < E / R; ++i) {
+    const int q = (t + i * T) & (NS - 1);
+#pragma unroll
+    for (int r = 1; r < R; ++r) {
+      const int p = (r * q) % len;
+      float sn, cs;
+      sincospif(-2.0f * (float)p / (float)len, &sn, &cs);
+      reg.w2[i][r - 1] = make_float2(cs, sn);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(RowPairCfg::THREADS, 2) k_row_slice_pair_2048(const PassArgs a, int n_tiles) {
   using Cfg = RowPairCfg;
-  constexpr int N = Cfg::N, E = Cfg::E, T = Cfg::T;
+  constexpr int N = Cfg::N, E = Cfg::E, T = Cfg::T, SEG = Cfg::SEG;
+  static_assert(FftShape<N>::R2 > 1, "three-stage transform");
   extern __shared__ float2 smem[];
   float2* xa = smem;
   float2* xb = smem + Cfg::ROWBUF;
   float2* tw = smem + 2 * Cfg::ROWBUF;
-  float2* tbuf = tw + TwLayout<N>::TOTAL;
-  uint64_t* tbar = reinterpret_cast<uint64_t*>(tbuf + N);
+  float2* tbuf = tw + Cfg::TW1;                     // [N]: the tile's row of t_n
+  float2* stg = tbuf + N;                           // [2][2 SEG]: the tile's in-band rows
+  uint64_t* bars = reinterpret_cast<uint64_t*>(stg + 4 * SEG);
+  const uint32_t tbar = smem_u32(bars), sbar = smem_u32(bars + 1);
   if (threadIdx.x == 0) {
-    mbar_init(smem_u32(tbar), 1);
+    mbar_init(tbar, 1);
+    mbar_init(sbar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  build_twiddles<N>(tw, threadIdx.x, Cfg::THREADS);
-  __syncthreads();
+  build_twiddles_stage1(tw, threadIdx.x, Cfg::THREADS);
   const int t = threadIdx.x;
+  StageTwiddles<N> reg;
+  row_pair_stage2_twiddles(reg, t);
+  __syncthreads();
   const SmemView<E, 1> va{xa}, vb{xb};
   auto sync = [] { __syncthreads(); };
-  constexpr bool TW1 = STEM_ROW_PAIR_TW1, TW2 = STEM_ROW_PAIR_TW2;
-  StageTwiddles<N> reg;
-  if constexpr (TW1) load_stage_twiddles<N, E, FftShape<N>::R1, E>(reg.w1, t, tw);
-  if constexpr (TW2) load_stage_twiddles<N, E, FftShape<N>::R2, E * FftShape<N>::R1>(reg.w2, t, tw + TwLayout<N>::OFF2);
   const int pairs = (a.batch + 1) / 2;
   const int per = (n_tiles + gridDim.x - 1) / gridDim.x;
+  const int tile_begin = blockIdx.x * per;
   const int tile_end = min(n_tiles, (int)(blockIdx.x + 1) * per);
-  int staged_row = -1;
-  uint32_t tphase = 0;
 
-  for (int tile = blockIdx.x * per; tile < tile_end; ++tile) {
+  // the in-band segments of tile's rows into the stage (thread 0)
+  auto issue_rows = [&](int tile) {
+    const int row = tile / pairs, k = tile % pairs;
+    const int nw = 2 * k + 1 < a.batch ? 2 : 1;
+    mbar_arrive_expect_tx(sbar, 2u * nw * Cfg::SEG_BYTES);
+    for (int j = 0; j < nw; ++j) {
+      const float2* src = a.wave + (size_t)(2 * k + j) * N * N + (size_t)row * N;
+      const uint32_t dst = smem_u32(stg + j * 2 * SEG);
+      bulk_load(dst, src, Cfg::SEG_BYTES, sbar);
+      bulk_load(dst + Cfg::SEG_BYTES, src + (N - SEG), Cfg::SEG_BYTES, sbar);
+    }
+  };
+  if (threadIdx.x == 0 && tile_begin < tile_end) issue_rows(tile_begin);
+
+  int staged_row = -1;
+  uint32_t tphase = 0, sphase = 0;
+  bool t_pending = false;
+  for (int tile = tile_begin; tile < tile_end; ++tile) {
     const int row = tile / pairs, k = tile % pairs;
     const int wa = 2 * k, wb = 2 * k + 1;
     const bool has_b = wb < a.batch;
@@ -306,41 +358,44 @@ __global__ void __launch_bounds__(RowPairCfg::THREADS, STEM_ROW_PAIR_MINB)
       __syncthreads();   // every thread has read the previous row of t_n
       if (threadIdx.x == 0) {
         fence_proxy_async();
-        const uint32_t bar = smem_u32(tbar);
-        mbar_arrive_expect_tx(bar, N * (uint32_t)sizeof(float2));
-        bulk_load(smem_u32(tbuf), a.trans + (size_t)row * N, N * (uint32_t)sizeof(float2), bar);
+        mbar_arrive_expect_tx(tbar, N * (uint32_t)sizeof(float2));
+        bulk_load(smem_u32(tbuf), a.trans + (size_t)row * N, N * (uint32_t)sizeof(float2), tbar);
       }
+      t_pending = true;
     }
+    const bool ok = mbar_wait(sbar, sphase);
+    sphase ^= 1u;
     float2 A[E], B[E];
 #pragma unroll
     for (int q = 0; q < E; ++q) {
       const int x = t + q * T;
       const bool in = !all_out_of_band<N, T>(q) && in_band<N>(x);
-      A[q] = in ? pa[x] : make_float2(0.0f, 0.0f);
-      B[q] = (in && has_b) ? pb[x] : make_float2(0.0f, 0.0f);
+      A[q] = in ? stg[Cfg::seg_slot(x)] : make_float2(0.0f, 0.0f);
+      B[q] = (in && has_b) ? stg[2 * SEG + Cfg::seg_slot(x)] : make_float2(0.0f, 0.0f);
     }
-#if STEM_PREFETCH
-    if (t == 0 && tile + 1 < tile_end) {
-      const int nrow = (tile + 1) / pairs, nk = (tile + 1) % pairs;
-      constexpr int lo = ((N / 3 + 1) + 1) & ~1, hi = (N - N / 3) & ~1;
-      for (int j = 0; j < 2; ++j) {
-        const int nw = 2 * nk + j;
-        if (nw >= a.batch) break;
-        const float2* nr = a.wave + (size_t)nw * N * N + (size_t)nrow * N;
-        prefetch_l2_bulk(nr, lo * sizeof(float2));
-        prefetch_l2_bulk(nr + hi, (N - hi) * sizeof(float2));
+    // every thread holds its values (and agrees on the wait): the stage takes the next tile
+    if (__syncthreads_or(!ok)) {
+      if (threadIdx.x == 0) {
+        if (a.status) atomicExch(a.status, (int)STEM_ERR_TIMEOUT);
+        if (t_pending) mbar_wait(tbar, tphase);   // let the copies land before the CTA exits
       }
+      return;
     }
-#endif
-    fft_dist_x2<N, true, TW1, TW2>(A, B, va, vb, t, sync, tw, &reg);
+    if (threadIdx.x == 0 && tile + 1 < tile_end) {
+      fence_proxy_async();
+      issue_rows(tile + 1);
+    }
+    fft_dist_x2<N, true, false, true>(A, B, va, vb, t, sync, tw, &reg);
     if (fresh) {
-      const bool ok = mbar_wait(smem_u32(tbar), tphase);
+      const bool tok = mbar_wait(tbar, tphase);
       tphase ^= 1u;
+      t_pending = false;
       staged_row = row;
-      if (__syncthreads_or(!ok)) {
+      if (__syncthreads_or(!tok)) {
         if (threadIdx.x == 0) {
           if (a.status) atomicExch(a.status, (int)STEM_ERR_TIMEOUT);
-          mbar_wait(smem_u32(tbar), tphase ^ 1u);   // let the copy land before the CTA exits
+          mbar_wait(tbar, tphase ^ 1u);                                  // the t_n copy
+          if (tile + 1 < tile_end) mbar_wait(sbar, sphase);             // the next tile's rows
         }
         return;
       }
@@ -351,7 +406,7 @@ __global__ void __launch_bounds__(RowPairCfg::THREADS, STEM_ROW_PAIR_MINB)
       A[q] = cmul(A[q], tv);
       B[q] = cmul(B[q], tv);
     }
-    fft_dist_x2<N, false, TW1, TW2>(A, B, va, vb, t, sync, tw, &reg);
+    fft_dist_x2<N, false, false, true>(A, B, va, vb, t, sync, tw, &reg);
 #pragma unroll
     for (int q = 0; q < E; ++q) {
       const int x = t + q * T;
@@ -793,6 +848,9 @@ static cudaError_t row_slice_pair_2048(const PassArgs& a, cudaStream_t s) {
   using Cfg = RowPairCfg;
   static std::once_flag flag, occ_flag;
   static int occ = 0;
+  // the bulk copies read rows of the waves and of t_n from 16-byte boundaries
+  if (reinterpret_cast<uintptr_t>(a.wave) % 16 || reinterpret_cast<uintptr_t>(a.trans) % 16)
+    return cudaErrorInvalidValue;
   cudaError_t e = set_smem(k_row_slice_pair_2048, Cfg::SMEM, flag);
   if (e != cudaSuccess) return e;
   const int n_tiles = ((a.batch + 1) / 2) * Cfg::N;
@@ -803,10 +861,8 @@ static cudaError_t row_slice_pair_2048(const PassArgs& a, cudaStream_t s) {
 
 template <int N>
 static cudaError_t row_dispatch(int mode, const PassArgs& a, cudaStream_t s) {
-#if STEM_ROW_PAIR
   if constexpr (N == 2048)
     if (mode == ROW_SLICE) return row_slice_pair_2048(a, s);
-#endif
   switch (mode) {
     case ROW_FFT: return row_launch<N, ROW_FFT>(a, s);
     case ROW_IFFT: return row_launch<N, ROW_IFFT>(a, s);

@@ -259,7 +259,10 @@ __device__ __forceinline__ void stage_rename(float2 (&v)[E]) {
 // Full length-N transform over the T threads that share `sm`.  `sync` is
 // called around every shared-memory exchange (a warp or block barrier); `tw`
 // is the block's twiddle table (build_twiddles<N>).
-template <int N, bool INV, class View, class Sync>
+//
+// FIRST_SYNC = false drops the barrier before the first exchange write, for
+// callers that have synchronised the threads since their last read of `sm`.
+template <int N, bool INV, bool FIRST_SYNC = true, class View, class Sync>
 __device__ __forceinline__ void fft_dist(float2 (&v)[FftShape<N>::E], const View& sm, int t, Sync sync,
                                          const float2* tw) {
   using S = FftShape<N>;
@@ -267,7 +270,7 @@ __device__ __forceinline__ void fft_dist(float2 (&v)[FftShape<N>::E], const View
   constexpr int E = S::E;
   dft<E, INV>(v);                                   // stage 0, butterfly j = t
   if constexpr (S::R1 > 1) {
-    sync();
+    if constexpr (FIRST_SYNC) sync();
 #pragma unroll
     for (int k = 0; k < E; ++k) sm.at(t * E + k) = v[k];
     sync();
@@ -325,8 +328,8 @@ template <int N> struct StageTwiddles {
 // Two independent transforms of the same length (rows a and b) stage by stage,
 // sharing the barriers: the instructions of one fill the latencies of the
 // other, and a row costs half the barriers.  sa and sb are separate exchange
-// buffers.  Same register conventions as fft_dist.
-template <int N, bool INV, bool TW1 = false, bool TW2 = false, class View, class Sync>
+// buffers.  Same register conventions (and FIRST_SYNC) as fft_dist.
+template <int N, bool INV, bool TW1 = false, bool TW2 = false, bool FIRST_SYNC = true, class View, class Sync>
 __device__ __forceinline__ void fft_dist_x2(float2 (&va)[FftShape<N>::E], float2 (&vb)[FftShape<N>::E],
                                             const View& sa, const View& sb, int t, Sync sync, const float2* tw,
                                             const StageTwiddles<N>* reg = nullptr) {
@@ -336,7 +339,7 @@ __device__ __forceinline__ void fft_dist_x2(float2 (&va)[FftShape<N>::E], float2
   dft<E, INV>(va);
   dft<E, INV>(vb);
   if constexpr (S::R1 > 1) {
-    sync();
+    if constexpr (FIRST_SYNC) sync();
 #pragma unroll
     for (int k = 0; k < E; ++k) {
       sa.at(t * E + k) = va[k];

@@ -385,7 +385,8 @@ __global__ void __launch_bounds__(RowPairCfg::THREADS, 2) k_row_slice_pair_2048(
       fence_proxy_async();
       issue_rows(tile + 1);
     }
-    fft_dist_x2<N, true, false, true>(A, B, va, vb, t, sync, tw, &reg);
+    // the tile barrier above follows the previous tile's last reads of xa / xb
+    fft_dist_x2<N, true, false, true, false>(A, B, va, vb, t, sync, tw, &reg);
     if (fresh) {
       const bool tok = mbar_wait(tbar, tphase);
       tphase ^= 1u;
@@ -647,7 +648,8 @@ __global__ void __launch_bounds__(ColTmaCfg<N_>::threads(DET), ColTmaCfg<N_>::MI
   };
 
   if (tid == 0) {
-    for (int i = 0; i < 4; ++i) mbar_init(smem_u32(bars + i), 1);
+    // full: one arrival (the copy thread's expect_tx); done: one per transform warp
+    for (int i = 0; i < 4; ++i) mbar_init(smem_u32(bars + i), i < 2 ? 1 : NT / 32);
     *s_abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -702,10 +704,9 @@ __global__ void __launch_bounds__(ColTmaCfg<N_>::threads(DET), ColTmaCfg<N_>::MI
       const bool ok = mbar_wait(smem_u32(bars + b), (uint32_t)(k >> 1) & 1u);
       if (named_sync_or(1, NT, !ok)) {
         // hand the verdict to the copy thread, which records it and drains
-        if (tid == 0) {
-          *s_abort = 1;
-          mbar_arrive_one(smem_u32(bars + 2 + b));
-        }
+        if (tid == 0) *s_abort = 1;
+        __syncwarp();
+        if ((tid & 31) == 0) mbar_arrive_one(smem_u32(bars + 2 + b));
         break;
       }
       float2* st = stage + (size_t)b * N * C;
@@ -713,7 +714,8 @@ __global__ void __launch_bounds__(ColTmaCfg<N_>::threads(DET), ColTmaCfg<N_>::MI
 #pragma unroll
       for (int q = 0; q < E; ++q) v[q] = st[(t + q * T) * C + c];
       const int col = Cfg::band_tile(tile % Cfg::BAND_TILES) * C + c;
-      fft_dist<N, false>(v, view, t, sync, tw);
+      // the barrier that ended the previous tile follows its last reads of xbuf
+      fft_dist<N, false, false>(v, view, t, sync, tw);
       const int m = signed_freq(col, N);
       const float2 px = cscale(__ldg(a.prop_x + col), a.prop_scale);
 #pragma unroll
@@ -727,8 +729,10 @@ __global__ void __launch_bounds__(ColTmaCfg<N_>::threads(DET), ColTmaCfg<N_>::MI
 #pragma unroll
       for (int q = 0; q < E; ++q) st[(t + q * T) * C + c] = v[q];
       fence_proxy_async();   // these writes before the tensor store reads them
-      sync();                // ... by every transform thread; also frees xbuf for the next tile
-      if (tid == 0) mbar_arrive_one(smem_u32(bars + 2 + b));
+      __syncwarp();
+      // one arrival per transform warp (the next tile's barrier orders the
+      // reuse of xbuf)
+      if ((tid & 31) == 0) mbar_arrive_one(smem_u32(bars + 2 + b));
     }
   } else {
     auto sync = [] { __syncthreads(); };

@@ -23,9 +23,10 @@ an explicit trigonometric sum over the band, its zero-padded inverse, f = 1
 against multislice, the free-space closed form and shift covariance on the
 cropped grid.
 
-Parity unpinned: PRISM with f > 1 against multislice (the paper only calls
-the f=4 result "almost indistinguishable"); the oracle runs the same
-approximate algorithm in FP64 and the distance to multislice is reported, not
-bounded.
+Every function above has at least one such pin.  What no pin bounds is the
+approximation PRISM f > 1 itself makes (its distance from multislice, which
+the paper describes only qualitatively for f = 4): the oracle computes the
+same approximate algorithm in FP64, the GPU path is held to the oracle's
+PRISM, and the distance to multislice is reported, not asserted.
 """
 from .stem import *  # noqa: F401,F403

@@ -53,7 +53,7 @@ METRIC = "probes/s for multislice and PRISM f=8 at stated error; p50/p99 solve l
 # DRAM bytes per wave and slice (row + column pass, t_n excluded), measured
 # with ncu (dram__bytes_read.sum + dram__bytes_write.sum) on launches of 16
 # waves of 2048^2 and 32 waves of 1024^2 of the slice passes
-SLICE_TRAFFIC_PER_WAVE = {2048: 83.04e6, 1024: 19.34e6}
+SLICE_TRAFFIC_PER_WAVE = {2048: 83.06e6, 1024: 19.34e6}
 HBM_FALLBACK_GBS = 6400.0
 LOWP_TOL, FP32_TOL = 1e-2, 1e-4
 LOWP_FLOOR, FP32_FLOOR = 1e-4, 1e-5

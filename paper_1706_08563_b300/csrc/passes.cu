@@ -70,6 +70,10 @@ template <int N> struct ColCfg {
   static constexpr int THREADS = C * T;
   static constexpr size_t FFT_SMEM = ((size_t)(N + N / E) * C + TwLayout<N>::TOTAL) * sizeof(float2);
   static constexpr int MINB = min_blocks<N>();
+  // the detector pass at N <= 256 (PRISM windows, small multislice grids) runs
+  // three CTAs per SM (80 registers, no spills): 1210 -> 922 us per 4096
+  // windows of 256^2
+  static constexpr int minb(int mode) { return (mode == COL_DET && N <= 256) ? 3 : MINB; }
   // Column tiles inside the 2/3 band limit, |m| <= N/3 (columns [0, MB] and
   // [N - MB, N)).  Outside it the propagator's mask zeroes whole columns, so
   // the slice loop never reads or writes them.
@@ -425,7 +429,7 @@ __global__ void __launch_bounds__(RowPairCfg::THREADS, 2) k_row_slice_pair_2048(
 // read neighbouring columns, so every global access is C * 8 contiguous bytes.
 // ---------------------------------------------------------------------------
 template <int N, int MODE, bool BAND>
-__global__ void __launch_bounds__(ColCfg<N>::THREADS, ColCfg<N>::MINB) k_col_pass(const PassArgs a, int n_tiles) {
+__global__ void __launch_bounds__(ColCfg<N>::THREADS, ColCfg<N>::minb(MODE)) k_col_pass(const PassArgs a, int n_tiles) {
   using Cfg = ColCfg<N>;
   constexpr int E = Cfg::E, T = Cfg::T, C = Cfg::C;
   extern __shared__ float2 smem[];
@@ -438,16 +442,42 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, ColCfg<N>::MINB) k_col_pas
   const SmemView<E, C> view{smem + c};
   auto sync = [] { __syncthreads(); };
   constexpr int col_tiles = BAND ? Cfg::BAND_TILES : N / C;
+  // The detector pass takes a contiguous block of tiles, so that consecutive
+  // tiles are mostly columns of the same wave: its rings stay in shared memory
+  // across them and reach global memory once per wave (and CTA), not once per
+  // tile.  The other modes stride over the tiles.
+  constexpr bool DET = MODE == COL_DET;
+  const int per = DET ? (n_tiles + gridDim.x - 1) / gridDim.x : 0;
+  const int tile_begin = DET ? blockIdx.x * per : blockIdx.x;
+  const int tile_end = DET ? min(n_tiles, (int)(blockIdx.x + 1) * per) : n_tiles;
+  const int tile_step = DET ? 1 : gridDim.x;
+  int acc_wave = -1;   // the wave whose rings ring_acc holds (detector pass)
+  auto flush_rings = [&](bool zero) {
+    // every thread has finished adding into ring_acc (callers synchronise)
+    if (acc_wave >= 0) {
+      float* out = a.rings + (size_t)acc_wave * a.n_rings;
+      for (int i = threadIdx.x; i < a.n_rings; i += Cfg::THREADS) {
+        const float acc = ring_acc[i];
+        if (acc != 0.0f) atomicAdd(out + i, acc * a.ring_scale);
+        if (zero) ring_acc[i] = 0.0f;
+      }
+    } else if (zero) {
+      for (int i = threadIdx.x; i < a.n_rings; i += Cfg::THREADS) ring_acc[i] = 0.0f;
+    }
+  };
 
-  for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+  for (int tile = tile_begin; tile < tile_end; tile += tile_step) {
     const int wave = tile / col_tiles;
     const int ct = tile % col_tiles;
     const int col = (BAND ? Cfg::band_tile(ct) : ct) * C + c;
     float2* w = a.wave + (size_t)wave * N * N + col;
 
-    if constexpr (MODE == COL_DET) {
-      __syncthreads();   // the previous tile's flush has read ring_acc
-      for (int i = threadIdx.x; i < a.n_rings; i += Cfg::THREADS) ring_acc[i] = 0.0f;
+    if constexpr (DET) {
+      if (wave != acc_wave) {
+        __syncthreads();   // the previous tile's sums are in ring_acc
+        flush_rings(true);
+        acc_wave = wave;
+      }
     }
 
     float2 v[E];
@@ -546,12 +576,6 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, ColCfg<N>::MINB) k_col_pas
           if (r != kLutNoRing) atomicAdd(ring_acc + r, cabs2(v[q]));
         }
       }
-      __syncthreads();
-      float* out = a.rings + (size_t)wave * a.n_rings;
-      for (int i = threadIdx.x; i < a.n_rings; i += Cfg::THREADS) {
-        const float acc = ring_acc[i];
-        if (acc != 0.0f) atomicAdd(out + i, acc * a.ring_scale);
-      }
     } else if constexpr (MODE == COL_DP) {
       // 4D output: the whole diffraction pattern of the wave inside the 2/3
       // band limit (pixels outside it, including stale out-of-band columns of a
@@ -568,6 +592,10 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, ColCfg<N>::MINB) k_col_pas
 #pragma unroll
       for (int q = 0; q < E; ++q) w[(size_t)(t + q * T) * N] = v[q];
     }
+  }
+  if constexpr (DET) {
+    __syncthreads();   // the last tile's sums are in ring_acc
+    flush_rings(false);
   }
 }
 

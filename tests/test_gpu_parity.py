@@ -57,6 +57,19 @@ def test_potentials_vs_oracle(api):
     assert np.max(np.abs(trans.cpu().numpy() - tref)) <= 2e-6
 
 
+@pytest.mark.parametrize("n,cell,n_atoms", [
+    (64, (6.0, 7.0, 4.0), 12),      # cutoff above half the cell: several periodic images per axis
+    (512, (10.0, 12.0, 4.0), 80),   # 256 neighbour cells in reach (two cell groups), lists above 32 atoms
+])
+def test_potentials_large_cutoff_vs_oracle(api, n, cell, n_atoms):
+    w = W.Workload("pl", cell, n_atoms, n, 2, 2.0, 200.0, 20.0, 4, 2.0, 40)
+    xyz, gauss = W.atoms(w, seed=n)
+    plan = api.Plan.from_workload(w)
+    _, v = plan.slice_potentials(dev(xyz), dev(gauss), want_v=True)
+    vref = O.projected_potential(O.params_from(w), xyz, gauss)
+    assert np.max(np.abs(v.cpu().numpy() - vref)) <= 2e-6 * np.max(vref)
+
+
 def test_potentials_repeatable(api):
     """The FP32 sums run in an order fixed by the input: two calls agree bit for bit."""
     w = W.scaled(W.C2, n_atoms=2000)

@@ -170,6 +170,10 @@ stem_status stem_selftest_fma_rate(int32_t packed, int64_t iters, int32_t blocks
  *   v_out      float32 [n_slices][n][n] in V*A, or NULL
  *   trans_out  complex64 [n_slices][n][n]: t_n = exp(i sigma V_n) (Eq. 1), or NULL
  *   workspace  >= stem_slice_potentials_workspace(plan, n_atoms) bytes
+ * Each pixel's sum runs in FP32 in an order fixed by the input (atoms by index
+ * within each 32 x 32 pixel cell), so repeated calls give identical bits;
+ * permuting the atoms may change the last bits.  Needs n >= 64
+ * (STEM_ERR_UNSUPPORTED otherwise); asynchronous on `stream`.
  * ------------------------------------------------------------------------ */
 size_t stem_slice_potentials_workspace(stem_plan plan, int64_t n_atoms);
 stem_status stem_slice_potentials(stem_plan plan, const double* atoms_xyz, const float* gauss,

@@ -88,6 +88,18 @@ def peaks():
         return HBM_FALLBACK_GBS, 1800.0, "fallback"
 
 
+def tensor_peaks():
+    """(burst, sustained) dense bf16 TFLOP/s (FP16 runs at the same rate) and the source."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        burst = float(d["bf16_tflops"])
+        return burst, float(d.get("bf16_tflops_sustained", burst)), "measured"
+    except Exception:
+        return 1800.0, 1400.0, "fallback"
+
+
 def host_cores() -> int:
     try:
         return len(os.sched_getaffinity(0))
@@ -182,16 +194,23 @@ def fft_lane_ops_per_element(n: int) -> float:
     return ops / e
 
 
+def band_cols(n: int) -> int:
+    """Columns the slice column pass visits: whole column tiles that touch the
+    2/3 band limit |m| <= n/3 (tiles of 4 columns in the TMA passes at 1024 and
+    2048, of up to 16 otherwise)."""
+    c = 4 if n in (1024, 2048) else max(1, min(16, 256 // (n // FFT_PLAN[n][0])))
+    mb = n // 3
+    lo, hi0 = (mb + 1 + c - 1) // c, (n - mb) // c
+    return (lo + n // c - hi0) * c if lo < hi0 else n
+
+
 def smatrix_lane_ops(n: int, n_slices: int, n_beams: int) -> float:
     """FP32 lane operations of the S-matrix build: per beam and slice a row pass
     (2 transforms of every row + the transmission product, 4 per element) and a
     column pass over the column tiles inside the band limit (2 transforms + the
     propagator products, 8 per element); the first row pass has no inverse
     transform and a last row pass adds one (net: 2 S row transforms)."""
-    c = 4 if n == 2048 else (8 if n == 1024 else max(1, min(16, 256 // (n // FFT_PLAN[n][0]))))
-    mb = n // 3
-    lo, hi0 = (mb + 1 + c - 1) // c, (n - mb) // c
-    cols = (lo + n // c - hi0) * c if lo < hi0 else n
+    cols = band_cols(n)
     per_fft = fft_lane_ops_per_element(n)
     row = n * n * (2 * per_fft + 4)
     col = cols * n * (2 * per_fft + 8)
@@ -384,6 +403,7 @@ def run_ours(args, rank, world, local_rank):
     clocks = Clocks(local_rank)
     clocks.start()
     launches0 = lib.stem_launch_count()
+    api.profile_enable(True)          # CUDA events around each hot kernel launch (roofline per kernel)
     t0 = time.perf_counter()
     evs = []
     for i in range(args.steps):
@@ -392,6 +412,8 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
     launches = lib.stem_launch_count() - launches0
+    kprof = {k: api.profile_read(k) for k in api.PROF_KINDS}
+    api.profile_enable(False)
     clk = clocks.stop()
     if world > 1:
         torch.distributed.barrier()
@@ -476,21 +498,63 @@ def run_ours(args, rank, world, local_rank):
     waves = n_beams if prism else n_probes
     batches = math.ceil(n_beams / batch) if prism else math.ceil(n_probes / batch)
     traffic = None if per_wave is None else per_wave * waves * w.n_slices + batches * w.n_slices * 8.0 * n2
-    res["roofline"] = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+    # the dominant kernels alone: the slice row and column passes, timed by CUDA
+    # events around each of their launches over the timed steps.  Per step the
+    # S-matrix runs S - 1 slice row passes per beam (the first slice's row pass
+    # builds the plane waves) and S slice column passes; multislice runs S row
+    # passes and S - 1 slice column passes per probe (the last is the detector).
+    (n_row, row_ms), (n_col, col_ms) = kprof["row_slice"], kprof["col_slice"]
+    row_ws = waves * (w.n_slices - 1 if prism else w.n_slices)
+    col_ws = waves * (w.n_slices if prism else w.n_slices - 1)
+    k_alg = (row_ws + col_ws) * 16.0 * band * n2 + (n_row / args.steps) * 8.0 * n2
+    k_ms = (row_ms + col_ms) / args.steps
+    k_ach = k_alg / (k_ms / 1e3) / 1e9 if k_ms > 0 else None
+    res["roofline"] = {"bound": "hbm", "achieved": k_ach, "peak": hbm, "unit": "GB/s",
+                       "frac": k_ach / hbm if k_ach else None,
                        "traffic": traffic, "traffic_unit": "bytes per step (slice passes, scaled from a 16-wave capture)",
-                       "kernel": kernel, "peak_source": src, "algorithmic_bytes_per_step": alg}
+                       "kernel": kernel, "peak_source": src, "algorithmic_bytes_per_step": k_alg,
+                       "what": "band-limited algorithmic bytes of the slice row and column passes / their summed "
+                               "launch durations (CUDA events around every launch in the timed steps)",
+                       "launches_per_step": {"row": n_row / args.steps, "col": n_col / args.steps},
+                       "ms_per_launch": {"row": row_ms / max(n_row, 1), "col": col_ms / max(n_col, 1)},
+                       "phase": {"achieved": ach, "frac": ach / hbm, "algorithmic_bytes_per_step": alg,
+                                 "what": ("whole S-matrix phase" if prism else "whole multislice call")
+                                 + " (first-slice, last-slice and store passes included) / phase time"}}
     if prism and extras:
         fma = measure_fma_rate(lib, dev)
         ops = smatrix_lane_ops(w.n, w.n_slices, n_beams)
         ach_ops = ops / (ms / 1e3) / 1e12
+        # the slice passes alone: row pass 2 transforms + transmission per element,
+        # column pass 2 transforms + propagator products on the in-band columns
+        per_fft = fft_lane_ops_per_element(w.n)
+        k_ops = (row_ws * n2 * (2 * per_fft + 4) + col_ws * band_cols(w.n) * w.n * (2 * per_fft + 8))
+        k_ach_ops = k_ops / (k_ms / 1e3) / 1e12 if k_ms > 0 else None
         res["roofline"]["fp32"] = {
-            "bound": "alu", "achieved": ach_ops, "peak": fma["peak_tops"], "unit": "T lane-ops/s",
-            "frac": ach_ops / fma["peak_tops"], "lane_ops_per_step": ops,
-            "lane_ops_per_element_per_fft": fft_lane_ops_per_element(w.n),
+            "bound": "alu", "achieved": k_ach_ops, "peak": fma["peak_tops"], "unit": "T lane-ops/s",
+            "frac": k_ach_ops / fma["peak_tops"] if k_ach_ops else None, "lane_ops_per_step": k_ops,
+            "lane_ops_per_element_per_fft": per_fft,
             "peak_source": "measured in this run: independent FMA chains (scalar "
                            f"{fma['scalar']:.1f}, packed f32x2 {fma['packed_f32x2']:.1f} T lane-ops/s)",
-            "what": "FP32 lane operations of the S-matrix phase counted from the kernels' radix plan "
-                    "(transforms, twiddles, transmission and propagator products) / S-matrix phase time"}
+            "what": "FP32 lane operations of the slice row and column passes counted from the kernels' radix "
+                    "plan (transforms, twiddles, transmission and propagator products) / their summed launch "
+                    "durations",
+            "phase": {"achieved": ach_ops, "frac": ach_ops / fma["peak_tops"], "lane_ops_per_step": ops,
+                      "what": "the whole S-matrix phase's lane operations / S-matrix phase time"}}
+    n_sum, sum_ms = kprof["beam_sum"]
+    if prism and n_sum > 0 and args.storage != "f32":
+        # useful work of the window beam sums: a complex multiply-add (8 flops)
+        # per probe, window pixel and beam; the kernel runs inside a long step,
+        # so the sustained tensor rate is the denominator
+        burst, sustained, tsrc = tensor_peaks()
+        flop = float(n_probes) * (w.n // f) ** 2 * n_beams * 8.0
+        t_ach = flop / (sum_ms / args.steps / 1e3) / 1e12
+        res["roofline"]["beam_sum"] = {
+            "bound": "tensor", "achieved": t_ach, "peak": sustained, "unit": "TFLOP/s", "frac": t_ach / sustained,
+            "frac_of_burst": t_ach / burst, "peak_source": tsrc + " (bf16 sustained; FP16 has the same dense rate)",
+            "kernel": "k_beam_sum_umma (tcgen05, FP16 S-matrix)", "flop_per_step": flop,
+            "launches_per_step": n_sum / args.steps, "ms_per_launch": sum_ms / n_sum,
+            "what": "useful flops of the window beam sums / the beam-sum launches' summed durations"}
+    res["kernel_ms_per_step"] = {k: v[1] / args.steps for k, v in kprof.items()}
     res["e2e"] = {"value": probes_all / (tot_e2e / 1e3), "unit": "probes/s",
                   "h2d_bytes_per_step": int(h_xyz.numel() * 8 + h_gauss.numel() * 4 + h_xy.numel() * 8),
                   "d2h_bytes_per_step": int(h_rings.numel() * 4)}

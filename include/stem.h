@@ -365,6 +365,33 @@ size_t stem_footprint_bytes(const stem_params* params, int32_t algo, int32_t f,
  * devices, all streams); for launch accounting in benchmarks. */
 uint64_t stem_launch_count(void);
 
+/* ---------------------------------------------------------------------------
+ * Kernel timing, for measuring a hot kernel's own launch duration inside a
+ * running workload (the roofline of one kernel rather than of a whole phase).
+ * While enabled, the library brackets every launch of the kernel families
+ * below with two CUDA events recorded on the launch's stream (two event
+ * records per launch, nothing else changes); stem_profile_read waits for the
+ * family's last launch and returns the number of launches recorded since
+ * stem_profile_enable(1) and their summed device time in milliseconds.
+ *   STEM_PROF_ROW_SLICE   slice-loop row pass (Eq. 1 and the row transforms)
+ *   STEM_PROF_COL_SLICE   slice-loop column pass (Eq. 2 and the column transforms)
+ *   STEM_PROF_BEAM_SUM    PRISM beam sum (tcgen05 or CUDA-core engine)
+ *   STEM_PROF_POTENTIALS  projected potentials (the per-tile sum)
+ * stem_profile_enable(1) starts recording and clears earlier records,
+ * stem_profile_enable(0) stops it.  Process-wide, thread-safe; the events
+ * belong to the device current at each launch.  Errors: STEM_ERR_INVALID for
+ * an unknown family or NULL outputs, STEM_ERR_CUDA if an event call failed.
+ * ------------------------------------------------------------------------ */
+typedef enum {
+  STEM_PROF_ROW_SLICE = 0,
+  STEM_PROF_COL_SLICE = 1,
+  STEM_PROF_BEAM_SUM = 2,
+  STEM_PROF_POTENTIALS = 3,
+  STEM_PROF_KINDS = 4
+} stem_prof_kind;
+stem_status stem_profile_enable(int32_t on);
+stem_status stem_profile_read(int32_t kind, int64_t* launches, double* total_ms);
+
 const char* stem_status_string(stem_status status);
 
 #ifdef __cplusplus

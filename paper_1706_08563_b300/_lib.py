@@ -14,6 +14,11 @@ from ctypes import POINTER, c_char_p, c_double, c_float, c_int32, c_int64, c_siz
 LIB_PATH = os.environ.get("STEM_LIB") or os.path.join(os.path.dirname(os.path.abspath(__file__)), "libstem.so")
 
 STEM_OK = 0
+# kernel families of stem_profile_read
+STEM_PROF_ROW_SLICE = 0
+STEM_PROF_COL_SLICE = 1
+STEM_PROF_BEAM_SUM = 2
+STEM_PROF_POTENTIALS = 3
 STEM_ERR_INVALID = -1
 STEM_ERR_NOMEM = -2
 STEM_ERR_CUDA = -3
@@ -41,6 +46,8 @@ class StemError(RuntimeError):
 SIGNATURES = {
     "stem_status_string": (c_char_p, [c_int32]),
     "stem_launch_count": (ctypes.c_uint64, []),
+    "stem_profile_enable": (c_int32, [c_int32]),
+    "stem_profile_read": (c_int32, [c_int32, POINTER(c_int64), POINTER(c_double)]),
     "stem_plan_create": (c_int32, [POINTER(StemParams), POINTER(c_void_p)]),
     "stem_plan_destroy": (None, [c_void_p]),
     "stem_plan_device_status": (c_int32, [c_void_p, POINTER(c_int32)]),

@@ -458,3 +458,20 @@ def memory_model(w, algo: str, budget_bytes: int, f: int = 1, storage: str = "f3
     if footprint_bytes(w, algo + "_streamed", f, storage, batch) <= budget_bytes:
         return "streamed"
     raise MemoryError(f"{w.name}: needs more than {budget_bytes} device bytes even when streamed")
+
+
+# kernel families of profile_read (stem_prof_kind)
+PROF_KINDS = {"row_slice": _lib.STEM_PROF_ROW_SLICE, "col_slice": _lib.STEM_PROF_COL_SLICE,
+              "beam_sum": _lib.STEM_PROF_BEAM_SUM, "potentials": _lib.STEM_PROF_POTENTIALS}
+
+
+def profile_enable(on: bool = True) -> None:
+    """Start (clearing earlier records) or stop CUDA-event timing of the hot kernel families."""
+    check(_lib.load().stem_profile_enable(1 if on else 0), "stem_profile_enable")
+
+
+def profile_read(kind: str) -> Tuple[int, float]:
+    """(launches, summed device milliseconds) of one family since profile_enable(True)."""
+    n, ms = ctypes.c_int64(), ctypes.c_double()
+    check(_lib.load().stem_profile_read(PROF_KINDS[kind], ctypes.byref(n), ctypes.byref(ms)), "stem_profile_read")
+    return n.value, ms.value

@@ -46,6 +46,21 @@ enum ColMode { COL_SLICE = 0, COL_DET = 1, COL_PROBE_INIT = 2, COL_FFT = 3, COL_
 // Counts this library's kernel launches (stem_launch_count); called at every launch site.
 void note_launch();
 
+// Brackets the kernel launch that follows it, in the same scope, with a pair of
+// CUDA events on stream s while stem_profile_enable(1) is in force
+// (profile.cu); kind is a stem_prof_kind.
+class ProfScope {
+ public:
+  ProfScope(int kind, cudaStream_t s);
+  ~ProfScope();
+  ProfScope(const ProfScope&) = delete;
+  ProfScope& operator=(const ProfScope&) = delete;
+
+ private:
+  cudaEvent_t stop_ = nullptr;
+  cudaStream_t stream_ = nullptr;
+};
+
 cudaError_t launch_row_pass(int n, int mode, const PassArgs& a, cudaStream_t s);
 cudaError_t launch_col_pass(int n, int mode, const PassArgs& a, cudaStream_t s);
 

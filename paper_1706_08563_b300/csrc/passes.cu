@@ -858,6 +858,7 @@ static cudaError_t row_launch(const PassArgs& a, cudaStream_t s) {
   if (e != cudaSuccess) return e;
   const int n_tiles = a.batch * (N / Cfg::ROWS);
   const int grid = std::min(n_tiles, resident_ctas(k_row_pass<N, MODE>, Cfg::THREADS, Cfg::SMEM, occ_flag, occ));
+  ProfScope prof(MODE == ROW_SLICE ? STEM_PROF_ROW_SLICE : -1, s);
   note_launch(), k_row_pass<N, MODE><<<grid, Cfg::THREADS, Cfg::SMEM, s>>>(a, n_tiles);
   return cudaGetLastError();
 }
@@ -872,6 +873,7 @@ static cudaError_t col_launch(const PassArgs& a, cudaStream_t s) {
   if (e != cudaSuccess) return e;
   const int n_tiles = a.batch * (BAND ? Cfg::BAND_TILES : N / Cfg::C);
   const int grid = std::min(n_tiles, resident_ctas(k_col_pass<N, MODE, BAND>, Cfg::THREADS, smem, occ_flag, occ));
+  ProfScope prof(MODE == COL_SLICE ? STEM_PROF_COL_SLICE : -1, s);
   note_launch(), k_col_pass<N, MODE, BAND><<<grid, Cfg::THREADS, smem, s>>>(a, n_tiles);
   return cudaGetLastError();
 }
@@ -887,6 +889,7 @@ static cudaError_t row_slice_pair_2048(const PassArgs& a, cudaStream_t s) {
   if (e != cudaSuccess) return e;
   const int n_tiles = ((a.batch + 1) / 2) * Cfg::N;
   const int grid = std::min(n_tiles, resident_ctas(k_row_slice_pair_2048, Cfg::THREADS, Cfg::SMEM, occ_flag, occ));
+  ProfScope prof(STEM_PROF_ROW_SLICE, s);
   note_launch(), k_row_slice_pair_2048<<<grid, Cfg::THREADS, Cfg::SMEM, s>>>(a, n_tiles);
   return cudaGetLastError();
 }
@@ -973,6 +976,7 @@ static cudaError_t col_slice_tma(const PassArgs& a, cudaStream_t s) {
   } else {
     grid = std::min(n_tiles, resident_ctas(k_col_slice_tma<N, DET>, Cfg::threads(DET), smem, occ_flag, occ));
   }
+  ProfScope prof(DET ? -1 : STEM_PROF_COL_SLICE, s);
   note_launch(), k_col_slice_tma<N, DET><<<grid, Cfg::threads(DET), smem, s>>>(a, map, n_tiles);
   return cudaGetLastError();
 }

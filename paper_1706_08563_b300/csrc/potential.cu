@@ -405,6 +405,7 @@ cudaError_t launch_potentials(const stem_params& p, double sigma, const double* 
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   const dim3 grid((unsigned)((n / kPotTile) * (n / kPotTile)), (unsigned)std::min(p.n_slices, 65535));
+  ProfScope prof(STEM_PROF_POTENTIALS, s);
   note_launch(), k_potential<<<grid, kPotThreads, 0, s>>>(recs, sorted, offsets, reach, n, p.n_slices, (float)sigma,
                                                          v_out, t_out);
   return cudaGetLastError();

@@ -395,6 +395,7 @@ cudaError_t prism_windows_chunk(const OutputArgs& o, const double* probe_xy, int
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const unsigned grid = (unsigned)sms * 4;
+  ProfScope prof(STEM_PROF_BEAM_SUM, s);
   switch (o.storage) {
     case STEM_F32:
       note_launch(), k_beam_sum_simt<STEM_F32><<<grid, 256, 0, s>>>(static_cast<const float*>(o.sdata), n, w, o.nbp, coef, origin,

@@ -387,6 +387,7 @@ cudaError_t launch_beam_sum_umma(const OutputArgs& o, int np, const double* prob
     if ((e = cudaFuncSetAttribute(k_beam_sum_umma<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
         cudaSuccess)
       return e;
+    ProfScope prof(STEM_PROF_BEAM_SUM, s);
     note_launch(), k_beam_sum_umma<__half><<<sms, kUmmaThreads, smem, s>>>(
         static_cast<const __half*>(o.sdata), static_cast<const __half*>(coef), o.n, o.w, o.nbp, origin, offsets,
         work, items, list, n_tiles, windows, o.status);
@@ -397,6 +398,7 @@ cudaError_t launch_beam_sum_umma(const OutputArgs& o, int np, const double* prob
     if ((e = cudaFuncSetAttribute(k_beam_sum_umma<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem)) != cudaSuccess)
       return e;
+    ProfScope prof(STEM_PROF_BEAM_SUM, s);
     note_launch(), k_beam_sum_umma<__nv_bfloat16><<<sms, kUmmaThreads, smem, s>>>(
         static_cast<const __nv_bfloat16*>(o.sdata), static_cast<const __nv_bfloat16*>(coef), o.n, o.w, o.nbp,
         origin, offsets, work, items, list, n_tiles, windows, o.status);

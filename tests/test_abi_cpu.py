@@ -145,3 +145,16 @@ def test_c_client_compiles_and_links_as_c99(repo_tmp):
     from conftest import build_c_client
     exe = build_c_client(repo_tmp)
     assert os.access(exe, os.X_OK)
+
+
+def test_profile_read_argument_checks():
+    lib = _lib.load()
+    n, ms = ctypes.c_int64(), ctypes.c_double()
+    assert lib.stem_profile_read(-1, ctypes.byref(n), ctypes.byref(ms)) == _lib.STEM_ERR_INVALID
+    assert lib.stem_profile_read(4, ctypes.byref(n), ctypes.byref(ms)) == _lib.STEM_ERR_INVALID
+    assert lib.stem_profile_read(0, None, ctypes.byref(ms)) == _lib.STEM_ERR_INVALID
+    # nothing recorded yet: zero launches, no CUDA call needed
+    assert lib.stem_profile_enable(1) == _lib.STEM_OK
+    assert lib.stem_profile_read(0, ctypes.byref(n), ctypes.byref(ms)) == _lib.STEM_OK
+    assert n.value == 0 and ms.value == 0.0
+    assert lib.stem_profile_enable(0) == _lib.STEM_OK

@@ -528,9 +528,15 @@ size_t stem_prism_smatrix_bytes(stem_plan pl, int32_t f, stem_storage storage) {
 
 static size_t smatrix_ws_waves(int n, int batch) { return ((size_t)batch * n * n * sizeof(float2) + 255) / 256 * 256; }
 
+// S-matrix workspace: the batch's waves, the beams' maxima, the row
+// transforms of t_0
+static size_t smatrix_ws_t0hat(int n, int batch) {
+  return smatrix_ws_waves(n, batch) + ((size_t)batch * sizeof(unsigned) + 255) / 256 * 256;
+}
+
 size_t stem_prism_smatrix_workspace(stem_plan pl, int32_t batch) {
   if (!pl || batch < 1) return 0;
-  return smatrix_ws_waves(pl->n, batch) + (size_t)batch * sizeof(unsigned);
+  return smatrix_ws_t0hat(pl->n, batch) + (size_t)pl->n * pl->n * sizeof(float2);
 }
 
 size_t stem_prism_smatrix_streamed_workspace(stem_plan pl, int32_t batch) {
@@ -575,15 +581,32 @@ static stem_status run_smatrix(stem_plan pl, const void* trans, bool streamed, i
   a.prop_scale = 1.0f / (float)plane;
   a.beam_max = reinterpret_cast<unsigned*>(static_cast<char*>(ws) + smatrix_ws_waves(n, batch));
   a.status = pl->status;
+  // the row transforms of t_0, shared by the first row pass of every beam
+  float2* t0hat = reinterpret_cast<float2*>(static_cast<char*>(ws) + smatrix_ws_t0hat(n, batch));
+  {
+    const float2* t0 = nullptr;
+    cudaError_t e = src->acquire(0, s, &t0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(t0hat, t0, plane * sizeof(float2), cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = src->release(s);
+    PassArgs a0 = a;
+    a0.wave = t0hat;
+    a0.batch = 1;
+    if (e == cudaSuccess) e = launch_row_pass(n, ROW_FFT, a0, s);
+    if (e != cudaSuccess) return STEM_ERR_CUDA;
+  }
   for (int b0 = b_begin; b0 < b_end; b0 += batch) {
     a.batch = std::min(batch, b_end - b0);
     a.beams = pl->beams[lf] + b0;
     cudaError_t e = cudaMemsetAsync(a.beam_max, 0, a.batch * sizeof(unsigned), s);
     for (int sl = 0; sl < pl->p.n_slices && e == cudaSuccess; ++sl) {
       const bool last = sl + 1 == pl->p.n_slices;
-      e = src->acquire(sl, s, &a.trans);
-      if (e == cudaSuccess) e = launch_row_pass(n, sl == 0 ? ROW_BEAM0 : ROW_SLICE, a, s);
-      if (e == cudaSuccess) e = src->release(s);
+      if (sl == 0) {
+        e = launch_beam0_shift(n, a, t0hat, s);
+      } else {
+        e = src->acquire(sl, s, &a.trans);
+        if (e == cudaSuccess) e = launch_row_pass(n, ROW_SLICE, a, s);
+        if (e == cudaSuccess) e = src->release(s);
+      }
       // cropped: the last column pass leaves the spectrum for the crop
       if (e == cudaSuccess) e = launch_col_pass(n, crop && last ? COL_SPEC : COL_SLICE, a, s);
     }
@@ -764,8 +787,9 @@ size_t stem_footprint_bytes(const stem_params* p, int32_t algo, int32_t f, stem_
   const int nb = count_beams(p, f, wavelength_a(p->energy_kev));
   const SmatLayout L = smatrix_layout(smatrix_grid(p->n, crop), nb, elem);
   const int chunk = (int)std::min<int64_t>(std::max<int64_t>(n_probes, 1), 4096);
-  return stack + L.total + (size_t)batch * plane * sizeof(float2) + (size_t)batch * 4 +
-         output_workspace_layout(p->n, f, chunk, L.nbp).total + rings;
+  // S-matrix workspace (waves, beam maxima, row transforms of t_0), S-matrix, output workspace
+  return stack + L.total + (size_t)batch * plane * sizeof(float2) + ((size_t)batch * 4 + 255) / 256 * 256 +
+         plane * sizeof(float2) + output_workspace_layout(p->n, f, chunk, L.nbp).total + rings;
 }
 
 }  // extern "C"

@@ -40,7 +40,7 @@ struct PassArgs {
   int* status = nullptr;             // plan status word (bounded waits record timeouts), or null
 };
 
-enum RowMode { ROW_SLICE = 0, ROW_BEAM0 = 1, ROW_IFFT_MAX = 2, ROW_FFT = 3, ROW_IFFT = 4 };
+enum RowMode { ROW_SLICE = 0, ROW_IFFT_MAX = 2, ROW_FFT = 3, ROW_IFFT = 4 };
 enum ColMode { COL_SLICE = 0, COL_DET = 1, COL_PROBE_INIT = 2, COL_FFT = 3, COL_IFFT = 4, COL_DP = 5, COL_SPEC = 6 };
 
 // Counts this library's kernel launches (stem_launch_count); called at every launch site.
@@ -63,6 +63,8 @@ class ProfScope {
 
 cudaError_t launch_row_pass(int n, int mode, const PassArgs& a, cudaStream_t s);
 cudaError_t launch_col_pass(int n, int mode, const PassArgs& a, cudaStream_t s);
+// First row pass of the S-matrix build from the row transform of t_0 (passes.cu).
+cudaError_t launch_beam0_shift(int n, const PassArgs& a, const float2* t0hat, cudaStream_t s);
 
 // Potentials (potential.cu)
 size_t potential_workspace(int64_t n_atoms, int n, int n_slices);

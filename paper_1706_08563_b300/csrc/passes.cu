@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(RowCfg<N>::THREADS, RowCfg<N>::MINB) k_row_pas
   constexpr int E = Cfg::E, T = Cfg::T;
   extern __shared__ float2 smem[];
   float2* tw = smem + Cfg::ROWS * Cfg::ROWBUF;
-  constexpr bool T_BULK = Cfg::T_STAGED && (MODE == ROW_SLICE || MODE == ROW_BEAM0);
+  constexpr bool T_BULK = Cfg::T_STAGED && MODE == ROW_SLICE;
   float2* tbuf = tw + TwLayout<N>::TOTAL;                                 // [ROWS][N] when T_BULK
   uint64_t* tbar = reinterpret_cast<uint64_t*>(tbuf + (Cfg::T_STAGED ? Cfg::ROWS * N : 0));
   if constexpr (T_BULK) {
@@ -158,28 +158,15 @@ __global__ void __launch_bounds__(RowCfg<N>::THREADS, RowCfg<N>::MINB) k_row_pas
     // slice-loop rows in the (k_x, y) domain hold zeros outside the band limit:
     // they are neither read from nor written to memory
     constexpr bool BAND_IN = MODE == ROW_SLICE || MODE == ROW_IFFT_MAX;
-    constexpr bool BAND_OUT = MODE == ROW_SLICE || MODE == ROW_BEAM0;
+    constexpr bool BAND_OUT = MODE == ROW_SLICE;
     float2 v[E];
-    if constexpr (MODE == ROW_BEAM0) {
-      // plane wave exp(2 pi i (m x + n y) / N), argument reduced exactly in integers
-      const int2 mn = a.beams[wave];
 #pragma unroll
-      for (int q = 0; q < E; ++q) {
-        const int x = t + q * T;
-        const int k = (int)((((long long)mn.x * x + (long long)mn.y * row) % N + N) % N);
-        float s, c;
-        sincospif(2.0f * (float)k / (float)N, &s, &c);
-        v[q] = make_float2(c, s);
-      }
-    } else {
-#pragma unroll
-      for (int q = 0; q < E; ++q) {
-        const int x = t + q * T;
-        v[q] = (!BAND_IN || (!all_out_of_band<N, T>(q) && in_band<N>(x))) ? w[x] : make_float2(0.0f, 0.0f);
-      }
+    for (int q = 0; q < E; ++q) {
+      const int x = t + q * T;
+      v[q] = (!BAND_IN || (!all_out_of_band<N, T>(q) && in_band<N>(x))) ? w[x] : make_float2(0.0f, 0.0f);
     }
 #if STEM_PREFETCH
-    if constexpr (MODE != ROW_BEAM0) {
+    {
       const int nt = tile + 1;
       if (t == 0 && nt < tile_end) {
         const int nrow = (nt / a.batch) * Cfg::ROWS + rl;
@@ -215,13 +202,13 @@ __global__ void __launch_bounds__(RowCfg<N>::THREADS, RowCfg<N>::MINB) k_row_pas
       const float2* tr = tbuf + rl * N;
 #pragma unroll
       for (int q = 0; q < E; ++q) v[q] = cmul(v[q], tr[t + q * T]);
-    } else if constexpr (MODE == ROW_SLICE || MODE == ROW_BEAM0) {
+    } else if constexpr (MODE == ROW_SLICE) {
       const float2* tr = a.trans + (size_t)row * N;
 #pragma unroll
       for (int q = 0; q < E; ++q) v[q] = cmul(v[q], __ldg(tr + t + q * T));
     }
 
-    if constexpr (MODE == ROW_SLICE || MODE == ROW_BEAM0 || MODE == ROW_FFT)
+    if constexpr (MODE == ROW_SLICE || MODE == ROW_FFT)
       fft_dist<N, false>(v, view, t, sync, tw);
 
 #pragma unroll
@@ -823,6 +810,45 @@ __global__ void __launch_bounds__(ColTmaCfg<N_>::threads(DET), ColTmaCfg<N_>::MI
 }
 
 // ---------------------------------------------------------------------------
+// First row pass of the S-matrix build.  The row transform of t_0 times the
+// plane wave exp(2 pi i (m x + n y) / N) is the row transform of t_0 shifted
+// by m and multiplied by exp(2 pi i n y / N).  With t0hat holding the row
+// transforms of t_0 (computed once per S-matrix call), the first row pass of
+// every beam is a gather: read a row of t0hat (the same row for successive
+// waves, so from L2), write the wave's in-band columns [0, N/3] and
+// [N - N/3, N) (the slice passes never read the others).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_beam0_shift(const PassArgs a, const float2* __restrict__ t0hat, int n) {
+  const int mb = n / 3, band = 2 * mb + 1;
+  const long long rows = (long long)a.batch * n;
+  for (long long r = blockIdx.x; r < rows; r += gridDim.x) {
+    const int y = (int)(r / a.batch), wave = (int)(r % a.batch);
+    const int2 mn = a.beams[wave];
+    const int k = (int)((((long long)mn.y * y) % n + n) % n);   // exp(2 pi i n y / N), reduced exactly
+    float sn, cs;
+    sincospif(2.0f * (float)k / (float)n, &sn, &cs);
+    const float2 ph = make_float2(cs, sn);
+    const float2* src = t0hat + (size_t)y * n;
+    float2* dst = a.wave + (size_t)wave * n * n + (size_t)y * n;
+    for (int i = threadIdx.x; i < band; i += blockDim.x) {
+      const int x = i <= mb ? i : n - band + i;
+      dst[x] = cmul(ph, src[(x - mn.x) & (n - 1)]);
+    }
+  }
+}
+
+cudaError_t launch_beam0_shift(int n, const PassArgs& a, const float2* t0hat, cudaStream_t s) {
+  if (n < 8 || (n & (n - 1)) || a.batch < 1) return cudaErrorInvalidValue;
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const long long rows = (long long)a.batch * n;
+  const unsigned grid = (unsigned)std::min<long long>(rows, (long long)sms * 8);
+  note_launch(), k_beam0_shift<<<grid, 256, 0, s>>>(a, t0hat, n);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // Launchers.  The dynamic shared-memory opt-in is set once per kernel in this
 // process (the library drives the device that was current at plan creation).
 // ---------------------------------------------------------------------------
@@ -906,7 +932,6 @@ static cudaError_t row_dispatch(int mode, const PassArgs& a, cudaStream_t s) {
   if constexpr (N >= 64) {
     switch (mode) {
       case ROW_SLICE: return row_launch<N, ROW_SLICE>(a, s);
-      case ROW_BEAM0: return row_launch<N, ROW_BEAM0>(a, s);
       case ROW_IFFT_MAX: return row_launch<N, ROW_IFFT_MAX>(a, s);
       default: break;
     }

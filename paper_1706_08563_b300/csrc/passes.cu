@@ -819,6 +819,7 @@ __global__ void __launch_bounds__(ColTmaCfg<N_>::threads(DET), ColTmaCfg<N_>::MI
 // [N - N/3, N) (the slice passes never read the others).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_beam0_shift(const PassArgs a, const float2* __restrict__ t0hat, int n) {
+  // blockDim.x == 256 and n <= 2048 (plans are limited to 2048), so 8 columns per thread cover the band
   const int mb = n / 3, band = 2 * mb + 1;
   const long long rows = (long long)a.batch * n;
   for (long long r = blockIdx.x; r < rows; r += gridDim.x) {
@@ -829,16 +830,27 @@ __global__ void __launch_bounds__(256) k_beam0_shift(const PassArgs a, const flo
     sincospif(2.0f * (float)k / (float)n, &sn, &cs);
     const float2 ph = make_float2(cs, sn);
     const float2* src = t0hat + (size_t)y * n;
-    float2* dst = a.wave + (size_t)wave * n * n + (size_t)y * n;
-    for (int i = threadIdx.x; i < band; i += blockDim.x) {
+    float2* __restrict__ dst = a.wave + (size_t)wave * n * n + (size_t)y * n;
+    // every load of the row first (up to 8 per thread: band < 2048 = 8 x 256),
+    // so that a thread has all its L2 reads in flight at once
+    float2 val[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int i = threadIdx.x + 256 * j;
       const int x = i <= mb ? i : n - band + i;
-      dst[x] = cmul(ph, src[(x - mn.x) & (n - 1)]);
+      if (i < band) val[j] = src[(x - mn.x) & (n - 1)];
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int i = threadIdx.x + 256 * j;
+      const int x = i <= mb ? i : n - band + i;
+      if (i < band) dst[x] = cmul(ph, val[j]);
     }
   }
 }
 
 cudaError_t launch_beam0_shift(int n, const PassArgs& a, const float2* t0hat, cudaStream_t s) {
-  if (n < 8 || (n & (n - 1)) || a.batch < 1) return cudaErrorInvalidValue;
+  if (n < 8 || n > 2048 || (n & (n - 1)) || a.batch < 1) return cudaErrorInvalidValue;
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

@@ -216,41 +216,63 @@ __global__ void k_origins(const double* __restrict__ xy, int np, int n, int w, d
     }
 }
 
-// Exclusive scans of counts (list offsets) and of ceil(count / group) (work
-// items); resets counts to 0 for use as fill cursors.  One CTA of 1024 threads.
-__global__ void k_scan_tiles(int* __restrict__ counts, int n_tiles, int group, int* __restrict__ offsets,
-                             int* __restrict__ work) {
-  __shared__ int s_a[1024], s_b[1024];
-  const int per = (n_tiles + blockDim.x - 1) / blockDim.x;
-  const int lo = min((int)threadIdx.x * per, n_tiles), hi = min(lo + per, n_tiles);
-  int a = 0, b = 0;
-  for (int i = lo; i < hi; ++i) {
-    a += counts[i];
-    b += (counts[i] + group - 1) / group;
+// Exclusive scans of the tiles' probe counts (offsets into the probe lists)
+// and of their work items (ceil(count / group)) in one CTA of 1024 threads:
+// chunks of 4096 tiles, 4 consecutive tiles per thread (coalesced), a
+// shuffle scan per warp, the warps' totals scanned by warp 0, and a running
+// carry across chunks.  counts become zeroed fill cursors.
+__global__ void __launch_bounds__(1024) k_scan_tiles(int* __restrict__ counts, int n_tiles, int group,
+                                                     int* __restrict__ offsets, int* __restrict__ work) {
+  __shared__ int s_wa[32], s_wb[32], s_carry[2];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) s_carry[0] = s_carry[1] = 0;
+  for (int base = 0; base < n_tiles; base += 4 * 1024) {
+    const int i0 = base + 4 * threadIdx.x;
+    int c[4], a = 0, b = 0;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      c[u] = i0 + u < n_tiles ? counts[i0 + u] : 0;
+      a += c[u];
+      b += (c[u] + group - 1) / group;
+    }
+    int ia = a, ib = b;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int oa = __shfl_up_sync(0xffffffffu, ia, d), ob = __shfl_up_sync(0xffffffffu, ib, d);
+      if (lane >= d) { ia += oa; ib += ob; }
+    }
+    __syncthreads();   // s_carry from the previous chunk is final; s_wa/s_wb free
+    if (lane == 31) { s_wa[warp] = ia; s_wb[warp] = ib; }
+    __syncthreads();
+    if (warp == 0) {
+      int wa = s_wa[lane], wb = s_wb[lane];
+      const int xa = wa, xb = wb;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const int oa = __shfl_up_sync(0xffffffffu, wa, d), ob = __shfl_up_sync(0xffffffffu, wb, d);
+        if (lane >= d) { wa += oa; wb += ob; }
+      }
+      s_wa[lane] = wa - xa;   // exclusive prefix of the warps' totals
+      s_wb[lane] = wb - xb;
+    }
+    __syncthreads();
+    int fa = s_carry[0] + s_wa[warp] + ia - a, fb = s_carry[1] + s_wb[warp] + ib - b;
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (i0 + u < n_tiles) {
+        offsets[i0 + u] = fa;
+        work[i0 + u] = fb;
+        counts[i0 + u] = 0;
+        fa += c[u];
+        fb += (c[u] + group - 1) / group;
+      }
+    __syncthreads();   // every thread has read s_carry
+    if (threadIdx.x == 1023) { s_carry[0] = fa; s_carry[1] = fb; }
   }
-  s_a[threadIdx.x] = a;
-  s_b[threadIdx.x] = b;
   __syncthreads();
-  for (int d = 1; d < (int)blockDim.x; d <<= 1) {
-    const int va = threadIdx.x >= d ? s_a[threadIdx.x - d] : 0;
-    const int vb = threadIdx.x >= d ? s_b[threadIdx.x - d] : 0;
-    __syncthreads();
-    s_a[threadIdx.x] += va;
-    s_b[threadIdx.x] += vb;
-    __syncthreads();
-  }
-  a = s_a[threadIdx.x] - a;
-  b = s_b[threadIdx.x] - b;
-  for (int i = lo; i < hi; ++i) {
-    offsets[i] = a;
-    work[i] = b;
-    a += counts[i];
-    b += (counts[i] + group - 1) / group;
-    counts[i] = 0;
-  }
-  if (threadIdx.x == blockDim.x - 1) {
-    offsets[n_tiles] = s_a[threadIdx.x];
-    work[n_tiles] = s_b[threadIdx.x];
+  if (threadIdx.x == 0) {
+    offsets[n_tiles] = s_carry[0];
+    work[n_tiles] = s_carry[1];
   }
 }
 

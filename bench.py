@@ -412,7 +412,11 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
     launches = lib.stem_launch_count() - launches0
-    kprof = {k: api.profile_read(k) for k in api.PROF_KINDS}
+    try:
+        kprof = {k: api.profile_read(k) for k in api.PROF_KINDS}
+    except Exception as exc:          # an event call failed: keep the phase-level roofline only
+        print(f"kernel timing unavailable: {exc}", file=sys.stderr)
+        kprof = {k: (0, 0.0) for k in api.PROF_KINDS}
     api.profile_enable(False)
     clk = clocks.stop()
     if world > 1:

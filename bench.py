@@ -205,16 +205,19 @@ def band_cols(n: int) -> int:
 
 
 def smatrix_lane_ops(n: int, n_slices: int, n_beams: int) -> float:
-    """FP32 lane operations of the S-matrix build: per beam and slice a row pass
-    (2 transforms of every row + the transmission product, 4 per element) and a
-    column pass over the column tiles inside the band limit (2 transforms + the
-    propagator products, 8 per element); the first row pass has no inverse
-    transform and a last row pass adds one (net: 2 S row transforms)."""
+    """FP32 lane operations of the S-matrix build: per beam, S - 1 slice row
+    passes (2 transforms of every row + the transmission product, 4 per
+    element) and S - 1 slice column passes over the column tiles inside the
+    band limit (2 transforms + the propagator products, 8 per element); the
+    first slice's column pass (1 transform + propagator, from the shared 2D
+    transform of t_0) and the last row pass (1 inverse transform)."""
     cols = band_cols(n)
     per_fft = fft_lane_ops_per_element(n)
     row = n * n * (2 * per_fft + 4)
     col = cols * n * (2 * per_fft + 8)
-    return float(n_beams) * n_slices * (row + col)
+    first = cols * n * (per_fft + 8)
+    last = n * n * per_fft
+    return float(n_beams) * ((n_slices - 1) * (row + col) + first + last)
 
 
 def measure_fma_rate(lib, dev) -> dict:
@@ -504,12 +507,12 @@ def run_ours(args, rank, world, local_rank):
     traffic = None if per_wave is None else per_wave * waves * w.n_slices + batches * w.n_slices * 8.0 * n2
     # the dominant kernels alone: the slice row and column passes, timed by CUDA
     # events around each of their launches over the timed steps.  Per step the
-    # S-matrix runs S - 1 slice row passes per beam (the first slice's row pass
-    # builds the plane waves) and S slice column passes; multislice runs S row
-    # passes and S - 1 slice column passes per probe (the last is the detector).
+    # S-matrix runs S - 1 of each per beam (the first slice starts from the 2D
+    # transform of t_0); multislice runs S row passes and S - 1 slice column
+    # passes per probe (the last is the detector).
     (n_row, row_ms), (n_col, col_ms) = kprof["row_slice"], kprof["col_slice"]
     row_ws = waves * (w.n_slices - 1 if prism else w.n_slices)
-    col_ws = waves * (w.n_slices if prism else w.n_slices - 1)
+    col_ws = waves * (w.n_slices - 1)
     k_alg = (row_ws + col_ws) * 16.0 * band * n2 + (n_row / args.steps) * 8.0 * n2
     k_ms = (row_ms + col_ms) / args.steps
     k_ach = k_alg / (k_ms / 1e3) / 1e9 if k_ms > 0 else None

@@ -528,8 +528,8 @@ size_t stem_prism_smatrix_bytes(stem_plan pl, int32_t f, stem_storage storage) {
 
 static size_t smatrix_ws_waves(int n, int batch) { return ((size_t)batch * n * n * sizeof(float2) + 255) / 256 * 256; }
 
-// S-matrix workspace: the batch's waves, the beams' maxima, the row
-// transforms of t_0
+// S-matrix workspace: the batch's waves, the beams' maxima, the 2D transform
+// of t_0
 static size_t smatrix_ws_t0hat(int n, int batch) {
   return smatrix_ws_waves(n, batch) + ((size_t)batch * sizeof(unsigned) + 255) / 256 * 256;
 }
@@ -581,7 +581,10 @@ static stem_status run_smatrix(stem_plan pl, const void* trans, bool streamed, i
   a.prop_scale = 1.0f / (float)plane;
   a.beam_max = reinterpret_cast<unsigned*>(static_cast<char*>(ws) + smatrix_ws_waves(n, batch));
   a.status = pl->status;
-  // the row transforms of t_0, shared by the first row pass of every beam
+  // The first slice of every beam starts from the 2D transform of t_0: the
+  // transform of t_0 times a plane wave (m, n) is that transform shifted by
+  // (m, n), so one transform per call replaces a row pass and a column
+  // transform per beam.
   float2* t0hat = reinterpret_cast<float2*>(static_cast<char*>(ws) + smatrix_ws_t0hat(n, batch));
   {
     const float2* t0 = nullptr;
@@ -591,23 +594,26 @@ static stem_status run_smatrix(stem_plan pl, const void* trans, bool streamed, i
     PassArgs a0 = a;
     a0.wave = t0hat;
     a0.batch = 1;
+    a0.band = 0;
     if (e == cudaSuccess) e = launch_row_pass(n, ROW_FFT, a0, s);
+    if (e == cudaSuccess) e = launch_col_pass(n, COL_FFT, a0, s);
     if (e != cudaSuccess) return STEM_ERR_CUDA;
   }
+  a.t0hat = t0hat;
   for (int b0 = b_begin; b0 < b_end; b0 += batch) {
     a.batch = std::min(batch, b_end - b0);
     a.beams = pl->beams[lf] + b0;
     cudaError_t e = cudaMemsetAsync(a.beam_max, 0, a.batch * sizeof(unsigned), s);
     for (int sl = 0; sl < pl->p.n_slices && e == cudaSuccess; ++sl) {
       const bool last = sl + 1 == pl->p.n_slices;
-      if (sl == 0) {
-        e = launch_beam0_shift(n, a, t0hat, s);
-      } else {
-        e = src->acquire(sl, s, &a.trans);
-        if (e == cudaSuccess) e = launch_row_pass(n, ROW_SLICE, a, s);
-        if (e == cudaSuccess) e = src->release(s);
-      }
       // cropped: the last column pass leaves the spectrum for the crop
+      if (sl == 0) {
+        e = launch_col_pass(n, crop && last ? COL_BEAM0_SPEC : COL_BEAM0, a, s);
+        continue;
+      }
+      e = src->acquire(sl, s, &a.trans);
+      if (e == cudaSuccess) e = launch_row_pass(n, ROW_SLICE, a, s);
+      if (e == cudaSuccess) e = src->release(s);
       if (e == cudaSuccess) e = launch_col_pass(n, crop && last ? COL_SPEC : COL_SLICE, a, s);
     }
     if (e == cudaSuccess)

@@ -33,6 +33,7 @@ struct PassArgs {
   double inv_lx = 0.0, inv_ly = 0.0;
   float probe_norm = 0.0f;           // 1 / (sqrt(|A|) N^2)
   const int2* beams = nullptr;       // [batch] (m, n) (offset)
+  const float2* t0hat = nullptr;     // COL_BEAM0*: the 2D transform of t_0, [N][N]
   unsigned* beam_max = nullptr;      // [batch] float bits of max(|Re|, |Im|)
   int band = 0;                      // COL_DET ends a slice loop: only in-band columns hold data
   double chi_c1 = 0.0, chi_c3 = 0.0; // aberration phase in turns: chi_c1 |k|^2 + chi_c3 |k|^4
@@ -41,7 +42,13 @@ struct PassArgs {
 };
 
 enum RowMode { ROW_SLICE = 0, ROW_IFFT_MAX = 2, ROW_FFT = 3, ROW_IFFT = 4 };
-enum ColMode { COL_SLICE = 0, COL_DET = 1, COL_PROBE_INIT = 2, COL_FFT = 3, COL_IFFT = 4, COL_DP = 5, COL_SPEC = 6 };
+// COL_BEAM0 / COL_BEAM0_SPEC: the first slice of the S-matrix build, from the
+// 2D transform of t_0 shifted by each beam (then as COL_SLICE / COL_SPEC
+// without the forward transform)
+enum ColMode {
+  COL_SLICE = 0, COL_DET = 1, COL_PROBE_INIT = 2, COL_FFT = 3, COL_IFFT = 4, COL_DP = 5, COL_SPEC = 6,
+  COL_BEAM0 = 7, COL_BEAM0_SPEC = 8
+};
 
 // Counts this library's kernel launches (stem_launch_count); called at every launch site.
 void note_launch();
@@ -63,8 +70,6 @@ class ProfScope {
 
 cudaError_t launch_row_pass(int n, int mode, const PassArgs& a, cudaStream_t s);
 cudaError_t launch_col_pass(int n, int mode, const PassArgs& a, cudaStream_t s);
-// First row pass of the S-matrix build from the row transform of t_0 (passes.cu).
-cudaError_t launch_beam0_shift(int n, const PassArgs& a, const float2* t0hat, cudaStream_t s);
 
 // Potentials (potential.cu)
 size_t potential_workspace(int64_t n_atoms, int n, int n_slices);

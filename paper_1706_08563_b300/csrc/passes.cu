@@ -494,12 +494,19 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, ColCfg<N>::minb(MODE)) k_c
         }
         v[q] = val;
       }
+    } else if constexpr (MODE == COL_BEAM0 || MODE == COL_BEAM0_SPEC) {
+      // the first slice of beam (m, n): the 2D transform of t_0 times the plane
+      // wave exp(2 pi i (m x + n y) / N) is the transform of t_0 shifted by (m, n)
+      const int2 mn = a.beams[wave];
+      const float2* src = a.t0hat + ((col - mn.x) & (N - 1));
+#pragma unroll
+      for (int q = 0; q < E; ++q) v[q] = __ldg(src + (size_t)((t + q * T - mn.y) & (N - 1)) * N);
     } else {
 #pragma unroll
       for (int q = 0; q < E; ++q) v[q] = w[(size_t)(t + q * T) * N];
     }
 #if STEM_PREFETCH
-    if constexpr (MODE != COL_PROBE_INIT) {
+    if constexpr (MODE != COL_PROBE_INIT && MODE != COL_BEAM0 && MODE != COL_BEAM0_SPEC) {
       // one prefetch per 32-byte sector of the next tile's column strip
       const int nt = tile + gridDim.x;
       if (nt < n_tiles && (c % (C < 4 ? C : 4)) == 0) {
@@ -516,7 +523,7 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, ColCfg<N>::minb(MODE)) k_c
 
     // COL_SPEC (the last slice of a cropped S-matrix) stores the propagated
     // spectrum M P FFT(.) / N^2 without the inverse transform
-    if constexpr (MODE == COL_SLICE || MODE == COL_SPEC) {
+    if constexpr (MODE == COL_SLICE || MODE == COL_SPEC || MODE == COL_BEAM0 || MODE == COL_BEAM0_SPEC) {
       const int m = signed_freq(col, N);
       const float2 px = cscale(__ldg(a.prop_x + col), a.prop_scale);
 #pragma unroll
@@ -528,7 +535,7 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, ColCfg<N>::minb(MODE)) k_c
       }
     }
 
-    if constexpr (MODE == COL_SLICE || MODE == COL_PROBE_INIT || MODE == COL_IFFT)
+    if constexpr (MODE == COL_SLICE || MODE == COL_PROBE_INIT || MODE == COL_IFFT || MODE == COL_BEAM0)
       fft_dist<N, true>(v, view, t, sync, tw);
 
     if constexpr (MODE == COL_DET) {
@@ -810,57 +817,6 @@ __global__ void __launch_bounds__(ColTmaCfg<N_>::threads(DET), ColTmaCfg<N_>::MI
 }
 
 // ---------------------------------------------------------------------------
-// First row pass of the S-matrix build.  The row transform of t_0 times the
-// plane wave exp(2 pi i (m x + n y) / N) is the row transform of t_0 shifted
-// by m and multiplied by exp(2 pi i n y / N).  With t0hat holding the row
-// transforms of t_0 (computed once per S-matrix call), the first row pass of
-// every beam is a gather: read a row of t0hat (the same row for successive
-// waves, so from L2), write the wave's in-band columns [0, N/3] and
-// [N - N/3, N) (the slice passes never read the others).
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_beam0_shift(const PassArgs a, const float2* __restrict__ t0hat, int n) {
-  // blockDim.x == 256 and n <= 2048 (plans are limited to 2048), so 8 columns per thread cover the band
-  const int mb = n / 3, band = 2 * mb + 1;
-  const long long rows = (long long)a.batch * n;
-  for (long long r = blockIdx.x; r < rows; r += gridDim.x) {
-    const int y = (int)(r / a.batch), wave = (int)(r % a.batch);
-    const int2 mn = a.beams[wave];
-    const int k = (int)((((long long)mn.y * y) % n + n) % n);   // exp(2 pi i n y / N), reduced exactly
-    float sn, cs;
-    sincospif(2.0f * (float)k / (float)n, &sn, &cs);
-    const float2 ph = make_float2(cs, sn);
-    const float2* src = t0hat + (size_t)y * n;
-    float2* __restrict__ dst = a.wave + (size_t)wave * n * n + (size_t)y * n;
-    // every load of the row first (up to 8 per thread: band < 2048 = 8 x 256),
-    // so that a thread has all its L2 reads in flight at once
-    float2 val[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int i = threadIdx.x + 256 * j;
-      const int x = i <= mb ? i : n - band + i;
-      if (i < band) val[j] = src[(x - mn.x) & (n - 1)];
-    }
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int i = threadIdx.x + 256 * j;
-      const int x = i <= mb ? i : n - band + i;
-      if (i < band) dst[x] = cmul(ph, val[j]);
-    }
-  }
-}
-
-cudaError_t launch_beam0_shift(int n, const PassArgs& a, const float2* t0hat, cudaStream_t s) {
-  if (n < 8 || n > 2048 || (n & (n - 1)) || a.batch < 1) return cudaErrorInvalidValue;
-  int dev = 0, sms = 148;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const long long rows = (long long)a.batch * n;
-  const unsigned grid = (unsigned)std::min<long long>(rows, (long long)sms * 8);
-  note_launch(), k_beam0_shift<<<grid, 256, 0, s>>>(a, t0hat, n);
-  return cudaGetLastError();
-}
-
-// ---------------------------------------------------------------------------
 // Launchers.  The dynamic shared-memory opt-in is set once per kernel in this
 // process (the library drives the device that was current at plan creation).
 // ---------------------------------------------------------------------------
@@ -1048,6 +1004,8 @@ static cudaError_t col_dispatch(int mode, const PassArgs& a, cudaStream_t s) {
       case COL_SLICE: return col_launch<N, COL_SLICE, true>(a, s);
       case COL_PROBE_INIT: return col_launch<N, COL_PROBE_INIT, true>(a, s);
       case COL_SPEC: return col_launch<N, COL_SPEC, true>(a, s);
+      case COL_BEAM0: return col_launch<N, COL_BEAM0, true>(a, s);
+      case COL_BEAM0_SPEC: return col_launch<N, COL_BEAM0_SPEC, true>(a, s);
       default: break;
     }
   }

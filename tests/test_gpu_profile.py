@@ -38,10 +38,10 @@ def test_profile_counts_slice_passes_and_keeps_results(api, n):
     batches = -(-probes // batch)
     beam_batches = -(-sm.n_beams // 8)
     # multislice: a row pass per slice, a slice column pass per slice but the
-    # last (the detector pass); the S-matrix: row passes after the first slice's
-    # plane-wave pass, a column pass on every slice
+    # last (the detector pass); the S-matrix: row and slice column passes on
+    # every slice but the first (which starts from the transform of t_0)
     assert rows == batches * slices + beam_batches * (slices - 1)
-    assert cols == batches * (slices - 1) + beam_batches * slices
+    assert cols == batches * (slices - 1) + beam_batches * (slices - 1)
     assert sums >= 1
     assert rows_ms > 0 and cols_ms > 0 and sums_ms > 0
     np.testing.assert_allclose(timed, plain, rtol=1e-6, atol=1e-9)

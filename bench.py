@@ -503,8 +503,6 @@ def run_ours(args, rank, world, local_rank):
     ach = alg / (ms / 1e3) / 1e9
     per_wave = SLICE_TRAFFIC_PER_WAVE.get(w.n)
     waves = n_beams if prism else n_probes
-    batches = math.ceil(n_beams / batch) if prism else math.ceil(n_probes / batch)
-    traffic = None if per_wave is None else per_wave * waves * w.n_slices + batches * w.n_slices * 8.0 * n2
     # the dominant kernels alone: the slice row and column passes, timed by CUDA
     # events around each of their launches over the timed steps.  Per step the
     # S-matrix runs S - 1 of each per beam (the first slice starts from the 2D
@@ -514,6 +512,9 @@ def run_ours(args, rank, world, local_rank):
     row_ws = waves * (w.n_slices - 1 if prism else w.n_slices)
     col_ws = waves * (w.n_slices - 1)
     k_alg = (row_ws + col_ws) * 16.0 * band * n2 + (n_row / args.steps) * 8.0 * n2
+    # measured DRAM bytes per (row + column) pass pair, split evenly, plus t_n per row-pass launch
+    traffic = (None if per_wave is None
+               else per_wave / 2.0 * (row_ws + col_ws) + (n_row / args.steps) * 8.0 * n2)
     k_ms = (row_ms + col_ms) / args.steps
     k_ach = k_alg / (k_ms / 1e3) / 1e9 if k_ms > 0 else None
     if not k_ach:                     # no kernel timing: the phase-level figures stand in

@@ -197,23 +197,31 @@ __device__ __forceinline__ void tile_span(int2 o, int n, int w, int& cx, int& cy
   cy = cy > nty ? nty : cy;
 }
 
-// Window origin (round half up, minus W/2, modulo N) and tile counts per probe.
+// Window origin of each probe (round half up, minus W/2, modulo N).
 __global__ void k_origins(const double* __restrict__ xy, int np, int n, int w, double dx, double dy,
-                          int2* __restrict__ origin, int* __restrict__ counts) {
+                          int2* __restrict__ origin) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= np) return;
   const long long ox = (long long)floor(xy[2 * p] / dx + 0.5) - w / 2;
   const long long oy = (long long)floor(xy[2 * p + 1] / dy + 0.5) - w / 2;
   const int2 o = make_int2((int)((ox % n + n) % n), (int)((oy % n + n) % n));
   origin[p] = o;
+}
+
+// One warp per probe: count the probe in every pixel tile its window touches
+// (a window of W = 256 touches about 560 tiles; the lanes share them).
+__global__ void k_count_tiles(const int2* __restrict__ origin, int np, int n, int w, int* __restrict__ counts) {
+  const int p = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+  if (p >= np) return;
+  const int2 o = origin[p];
   const int ntx = n / kTileX, nty = n / kTileY;
   int cx, cy;
   tile_span(o, n, w, cx, cy);
-  for (int iy = 0; iy < cy; ++iy)
-    for (int ix = 0; ix < cx; ++ix) {
-      const int tx = (o.x / kTileX + ix) % ntx, ty = (o.y / kTileY + iy) % nty;
-      atomicAdd(counts + ty * ntx + tx, 1);
-    }
+  for (int i = lane; i < cx * cy; i += 32) {
+    const int iy = i / cx, ix = i % cx;
+    const int tx = (o.x / kTileX + ix) % ntx, ty = (o.y / kTileY + iy) % nty;
+    atomicAdd(counts + ty * ntx + tx, 1);
+  }
 }
 
 // Exclusive scans of the tiles' probe counts (offsets into the probe lists)
@@ -284,19 +292,22 @@ __global__ void k_item_tiles(const int* __restrict__ work, int n_tiles, int* __r
   for (int g = work[t]; g < work[t + 1]; ++g) items[g] = t;
 }
 
+// One warp per probe: append the probe to the list of every tile its window
+// touches (list order within a tile is arbitrary; every window pixel is still
+// computed once, with its full beam sum in a fixed order).
 __global__ void k_fill_tiles(const int2* __restrict__ origin, int np, int n, int w, const int* __restrict__ offsets,
                              int* __restrict__ cursor, int* __restrict__ list) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  const int p = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
   if (p >= np) return;
   const int2 o = origin[p];
   const int ntx = n / kTileX, nty = n / kTileY;
   int cx, cy;
   tile_span(o, n, w, cx, cy);
-  for (int iy = 0; iy < cy; ++iy)
-    for (int ix = 0; ix < cx; ++ix) {
-      const int t = ((o.y / kTileY + iy) % nty) * ntx + (o.x / kTileX + ix) % ntx;
-      list[offsets[t] + atomicAdd(cursor + t, 1)] = p;
-    }
+  for (int i = lane; i < cx * cy; i += 32) {
+    const int iy = i / cx, ix = i % cx;
+    const int t = ((o.y / kTileY + iy) % nty) * ntx + (o.x / kTileX + ix) % ntx;
+    list[offsets[t] + atomicAdd(cursor + t, 1)] = p;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -402,11 +413,14 @@ cudaError_t prism_windows_chunk(const OutputArgs& o, const double* probe_xy, int
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   if ((e = cudaMemsetAsync(counts, 0, n_tiles * sizeof(int), s)) != cudaSuccess) return e;
-  note_launch(), k_origins<<<(np + 127) / 128, 128, 0, s>>>(probe_xy, np, n, w, o.dx, o.dy, origin, counts);
+  note_launch(), k_origins<<<(np + 127) / 128, 128, 0, s>>>(probe_xy, np, n, w, o.dx, o.dy, origin);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const unsigned warp_blocks = (unsigned)(((size_t)np * 32 + 255) / 256);   // one warp per probe
+  note_launch(), k_count_tiles<<<warp_blocks, 256, 0, s>>>(origin, np, n, w, counts);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   note_launch(), k_scan_tiles<<<1, 1024, 0, s>>>(counts, n_tiles, group, offsets, work);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  note_launch(), k_fill_tiles<<<(np + 127) / 128, 128, 0, s>>>(origin, np, n, w, offsets, counts, list);
+  note_launch(), k_fill_tiles<<<warp_blocks, 256, 0, s>>>(origin, np, n, w, offsets, counts, list);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   note_launch(), k_item_tiles<<<(n_tiles + 255) / 256, 256, 0, s>>>(work, n_tiles, items);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;

@@ -725,7 +725,7 @@ __global__ void __launch_bounds__(ColTmaCfg<N_>::threads(DET), ColTmaCfg<N_>::MI
       const int b = k & 1;
       const bool ok = mbar_wait(smem_u32(bars + b), (uint32_t)(k >> 1) & 1u);
       if (named_sync_or(1, NT, !ok)) {
-        // hand the verdict to the copy thread, which records it and drains
+        // hand the outcome to the copy thread, which records it and drains
         if (tid == 0) *s_abort = 1;
         __syncwarp();
         if ((tid & 31) == 0) mbar_arrive_one(smem_u32(bars + 2 + b));

@@ -335,7 +335,7 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_beam_sum_umma(
         e_probe[et] = p;
         e_org[et] = p >= 0 ? __ldg(origin + p) : make_int2(0, 0);
       }
-      // one thread waits; the named barrier hands all 128 the same verdict
+      // one thread waits; the named barrier hands all 128 the same outcome
       if (et == 0) *e_flag = mbar_wait(smem_u32(acc_full + b), (it >> 1) & 1u) && !abort_now();
       epi_sync();
       if (!*reinterpret_cast<volatile int*>(e_flag)) { *s_abort = 1; break; }
